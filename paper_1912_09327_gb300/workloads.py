@@ -1,0 +1,146 @@
+"""Seeded synthetic inputs shared by the tests, the smoke check and the bench.
+
+This module holds geometry and initial-state generators only: it contains none
+of the LBMTau1 arithmetic, so both the CUDA path and the CPU oracle can take
+their inputs from it.  Arrays are ``[ny, nx]`` row-major (``idx = y*nx + x``).
+
+Node types (the ``F`` flag array of Section 2.1, widened to three values):
+0 fluid, 1 solid no-slip wall (Eq. feqnoslip), 2 fixed-equilibrium node (the
+moving lid of the cavity in Section 3).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+FLUID, SOLID, FIXED = 0, 1, 2
+NU = 1.0 / 6.0  # lattice viscosity at tau = 1, Eq. (viscosity) with c_s^2 = 1/3
+
+
+@dataclass
+class Problem:
+    """A domain: node types, periodicity, body force and initial moments."""
+    name: str
+    mask: np.ndarray                     # uint8 [ny, nx]
+    periodic: tuple = (False, False)
+    force: tuple = (0.0, 0.0)
+    rho: np.ndarray = None               # float64 [ny, nx] density
+    jx: np.ndarray = None                # float64 [ny, nx] x momentum rho*u_x
+    jy: np.ndarray = None                # float64 [ny, nx] y momentum rho*u_y
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def shape(self):
+        return self.mask.shape
+
+    def state(self):
+        return self.rho.copy(), self.jx.copy(), self.jy.copy()
+
+
+def _rest_state(shape):
+    return np.ones(shape), np.zeros(shape), np.zeros(shape)
+
+
+def channel(nx: int = 64, ny: int = 32, u_max: float = 0.01) -> Problem:
+    """Poiseuille channel of Section 3: periodic in x, no-slip rows y = 0 and
+    y = ny - 1, driven by a body force chosen so that the plane-Poiseuille
+    centre-line speed is ``u_max``: f = 8 nu u_max / H^2, H = ny - 1 (walls on
+    the solid node centres)."""
+    mask = np.zeros((ny, nx), np.uint8)
+    mask[0, :] = SOLID
+    mask[-1, :] = SOLID
+    H = ny - 1
+    fx = 8.0 * NU * u_max / (H * H)
+    r, u, v = _rest_state(mask.shape)
+    return Problem("channel", mask, (True, False), (fx, 0.0), r, u, v,
+                   {"u_max": u_max, "H": H})
+
+
+def cavity(n: int = 1024, u_lid: float = 0.1, ny: int | None = None) -> Problem:
+    """Lid-driven cavity of Section 3 / Appendix A: walls at x = 0, x = nx-1,
+    y = 0 and the two top corners; the top row y = ny-1 (x = 1..nx-2) holds
+    fixed nodes with density 1 and momentum (u_lid, 0)."""
+    nx = n
+    ny = n if ny is None else ny
+    mask = np.zeros((ny, nx), np.uint8)
+    mask[:, 0] = SOLID
+    mask[:, -1] = SOLID
+    mask[0, :] = SOLID
+    mask[-1, 1:-1] = FIXED
+    r, u, v = _rest_state(mask.shape)
+    u[-1, 1:-1] = u_lid
+    return Problem("cavity", mask, (False, False), (0.0, 0.0), r, u, v,
+                   {"u_lid": u_lid, "Re": u_lid * (nx - 2) / NU})
+
+
+def porous(n: int = 4096, seed: int = 0, r_min: int = 8, r_max: int = 24,
+           solid_fraction: float = 0.30, fx: float = 1e-5,
+           ny: int | None = None, max_tries: int = 2_000_000) -> Problem:
+    """Periodic porous sample: non-overlapping discs with integer radii drawn
+    uniformly from [r_min, r_max], placed by random sequential addition with
+    periodic minimum-image distances, until the solid fraction reaches
+    ``solid_fraction``.  A node is solid when its centre lies within a disc."""
+    nx = n
+    ny = n if ny is None else ny
+    rng = np.random.default_rng(seed)
+    mask = np.zeros((ny, nx), np.uint8)
+    cx = np.empty(0); cy = np.empty(0); cr = np.empty(0)
+    tries = 0
+    while mask.mean() < solid_fraction and tries < max_tries:
+        tries += 1
+        r = int(rng.integers(r_min, r_max + 1))
+        x0 = rng.uniform(0, nx); y0 = rng.uniform(0, ny)
+        if cx.size:
+            dx = np.abs(cx - x0); dx = np.minimum(dx, nx - dx)
+            dy = np.abs(cy - y0); dy = np.minimum(dy, ny - dy)
+            if np.any(dx * dx + dy * dy <= (cr + r + 1.0) ** 2):
+                continue
+        cx = np.append(cx, x0); cy = np.append(cy, y0); cr = np.append(cr, r)
+        xs = np.arange(math.floor(x0 - r), math.ceil(x0 + r) + 1)
+        ys = np.arange(math.floor(y0 - r), math.ceil(y0 + r) + 1)
+        X, Y = np.meshgrid(xs, ys)
+        inside = (X - x0) ** 2 + (Y - y0) ** 2 <= r * r
+        mask[Y[inside] % ny, X[inside] % nx] = SOLID
+    rr, u, v = _rest_state(mask.shape)
+    return Problem("porous", mask, (True, True), (fx, 0.0), rr, u, v,
+                   {"discs": int(cx.size), "solid_fraction": float(mask.mean()),
+                    "mean_diameter": float(2 * cr.mean()) if cr.size else 0.0})
+
+
+def periodic_box(nx: int, ny: int, seed: int = 0, amp: float = 1e-3) -> Problem:
+    """Fully periodic, all-fluid box with a small random perturbation:
+    delta rho ~ amp N(0,1), u ~ amp N(0,1)."""
+    mask = np.zeros((ny, nx), np.uint8)
+    r, u, v = random_state((ny, nx), seed, amp)
+    return Problem("periodic", mask, (True, True), (0.0, 0.0), r, u, v)
+
+
+def random_state(shape, seed: int = 0, amp: float = 1e-3):
+    """(rho, rho*u_x, rho*u_y) with rho = 1 + amp N(0,1), u = amp N(0,1)."""
+    rng = np.random.default_rng(seed)
+    rho = 1.0 + amp * rng.standard_normal(shape)
+    ux = amp * rng.standard_normal(shape)
+    uy = amp * rng.standard_normal(shape)
+    return rho, rho * ux, rho * uy
+
+
+def random_mask(shape, seed: int = 0, p_solid: float = 0.2,
+                p_fixed: float = 0.0) -> np.ndarray:
+    """Independent random node types: solid with p_solid, fixed with p_fixed."""
+    rng = np.random.default_rng(seed)
+    u = rng.random(shape)
+    mask = np.zeros(shape, np.uint8)
+    mask[u < p_solid] = SOLID
+    mask[(u >= p_solid) & (u < p_solid + p_fixed)] = FIXED
+    return mask
+
+
+def random_problem(nx: int, ny: int, seed: int = 0, p_solid: float = 0.2,
+                   p_fixed: float = 0.05, amp: float = 0.02,
+                   periodic=(True, True), force=(1e-4, -5e-5)) -> Problem:
+    """Random node types and a random state: the general parity case."""
+    mask = random_mask((ny, nx), seed, p_solid, p_fixed)
+    r, u, v = random_state((ny, nx), seed + 1, amp)
+    return Problem("random", mask, tuple(periodic), tuple(force), r, u, v)
