@@ -1,0 +1,415 @@
+"""Benchmark of the LBMTau1 D2Q9 step on GB300.
+
+One bench step is one full LBMTau1 time step over the whole domain through the
+C ABI (``lbm_step(ctx, 1)``): the fused pull / equilibrium / wall rule /
+moment accumulation kernel with its fused residual and mass reduction, plus
+the one-block FP64 finalize kernel.
+
+Workload: the lid-driven cavity of Section 3 (walls on three sides, a fixed
+lid row moving at u = 0.1), FP32 storage, at the largest size of the
+256^2 .. 16384^2 single-domain sweep, 16384^2 nodes (6.7 GB of fields and node
+types, far larger than the 129 MB L2, so no L2 flush is needed between steps).
+Smaller sweep sizes, including the 1024^2 cavity itself, are reported beside
+it; those that fit in L2 are marked as such and say nothing about HBM.
+
+Multi-GPU: the step does not shard here (one domain per GPU); ``--gpus N``
+under torchrun runs N independent replicas (weak scaling) and reports the sum
+of their throughputs over the slowest rank's time.
+
+``--impl reference`` times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload (per step, one oracle step over the top 256 rows of the cavity, full
+width), so that the default 2000 steps end within a few minutes.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "D2Q9 LBMTau1 MLUPS & % HBM roofline; batched solves/s, p99 vs plain"
+UNIT = "MLUPS"
+BYTES_PER_LUP = 25          # read + write rho-1, jx, jy (FP32) + 1 B node type
+FALLBACK_HBM_GBS = 6800.0   # used only when MEASURED_PEAKS.json is absent
+KERNEL_SRC = os.path.join(ROOT, "paper_1912_09327_gb300", "csrc", "lbm_step.cu")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "lbm_step_kernel_f32.traffic.txt")
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--size", type=int, default=16384)
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args(argv)
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def max_over_ranks(value: float, world: int) -> float:
+    """Slowest rank's time (the whole job ends when the last replica does)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def load_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            d = json.load(open(path))
+            for k in ("hbm_gbs", "hbm_GBs", "hbm_copy_gbs"):
+                if k in d:
+                    return float(d[k]), "measured (MEASURED_PEAKS.json %s)" % k
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "fallback (no MEASURED_PEAKS.json)"
+
+
+def kernel_hash():
+    return hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
+
+
+def load_traffic(nodes):
+    """DRAM bytes per launch from the committed ncu summary, scaled to this
+    domain by its node count; None when the kernel changed since."""
+    if not os.path.exists(TRAFFIC_FILE):
+        return None
+    kv = {}
+    for line in open(TRAFFIC_FILE):
+        if ":" in line and not line.startswith("#"):
+            k, v = line.split(":", 1)
+            kv[k.strip()] = v.strip()
+    if kv.get("kernel_source_sha256_16") != kernel_hash():
+        return None
+    try:
+        return float(kv["dram_bytes_per_node"]) * nodes
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = float(f[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"],
+                    "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def time_steps(dom, stream, steps):
+    """Per-step CUDA-event durations (ms) of lbm_step(ctx, 1) on the domain's
+    stream."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for a, b in ev:
+        a.record(stream)
+        dom.step(1)
+        b.record(stream)
+    stream.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def cavity_domain(binding, n, stream):
+    from paper_1912_09327_gb300 import workloads as wl
+    p = wl.cavity(n, 0.1)
+    d = binding.Domain(n, n, p.periodic, p.force, stream=stream)
+    d.set_geometry(p.mask)
+    d.set_moments(p.rho, p.jx, p.jy)
+    return d, p
+
+
+def run_sweep(binding, stream, sizes, steps=200):
+    out = {}
+    import torch
+    l2 = torch.cuda.get_device_properties(0).L2_cache_size
+    for n in sizes:
+        d, _ = cavity_domain(binding, n, stream)
+        d.step(20)
+        stream.synchronize()
+        s = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        d.step(steps)
+        e.record(stream)
+        stream.synchronize()
+        ms = s.elapsed_time(e)
+        ws = BYTES_PER_LUP * n * n
+        out[str(n)] = {"mlups": round(n * n * steps / (ms * 1e3), 1),
+                       "gbs_algorithmic": round(ws / (ms / steps) / 1e6, 1),
+                       "l2_resident": bool(2 * ws < l2)}
+        d.close()
+        del d
+        torch.cuda.empty_cache()
+    return out
+
+
+def run_e2e(binding, dom, n, steps):
+    """Same metric through the public API with host buffers: per step, the
+    exact state goes host -> device from pinned memory (lbm_set_state), one
+    lbm_step, the state comes back (lbm_get_state) and the residual is read
+    (lbm_residual); wall-clock time with the copies inside."""
+    import torch
+    bufs_in = [torch.empty((n, n), dtype=torch.float32, pin_memory=True)
+               for _ in range(3)]
+    bufs_out = [torch.empty((n, n), dtype=torch.float32, pin_memory=True)
+                for _ in range(3)]
+    binding.lbm_get_state(dom.ctx, *bufs_in)
+    binding.lbm_set_state(dom.ctx, *bufs_in)
+    dom.step(1)
+    dom.residual()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        binding.lbm_set_state(dom.ctx, *bufs_in)
+        dom.step(1)
+        binding.lbm_get_state(dom.ctx, *bufs_out)
+        dom.residual()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    h2d = 3 * 4 * n * n
+    d2h = 3 * 4 * n * n + 32
+    return {"value": round(n * n * steps / dt / 1e6, 1), "unit": UNIT,
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "steps": steps,
+            "api": "lbm_set_state + lbm_step(1) + lbm_get_state + lbm_residual, pinned host"}
+
+
+def cpu_baseline(size, rows=1024, seconds=10.0):
+    """The FP64 oracle as it stands, on all host cores, on a bounded sample:
+    whole steps over the top `rows` rows of the size x size cavity (full
+    width), repeated until about `seconds` of CPU time have passed."""
+    import oracle
+    from paper_1912_09327_gb300 import workloads as wl
+    p = wl.cavity(size, 0.1, ny=rows)
+    oracle.build()
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    R, U, V = p.state()
+    oracle.run(p.mask, R, U, V, 1, p.periodic, p.force)   # warm-up
+    steps = 0
+    t0 = time.perf_counter()
+    while steps < 2 or time.perf_counter() - t0 < seconds:
+        R, U, V = oracle.run(p.mask, R, U, V, 1, p.periodic, p.force)
+        steps += 1
+    dt = time.perf_counter() - t0
+    return {"value": round(size * rows * steps / dt / 1e6, 2), "unit": UNIT,
+            "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": "%d steps of the top %d rows (full width %d) of the "
+                      "lid-driven cavity, FP64 C oracle, OpenMP over rows"
+                      % (steps, rows, size)}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    from paper_1912_09327_gb300 import workloads as wl
+    import oracle
+    oracle.build()
+    size, rows = args.size, 256
+    p = wl.cavity(size, 0.1, ny=rows)
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    R, U, V = p.state()
+    for _ in range(max(args.warmup, 0)):
+        R, U, V = oracle.run(p.mask, R, U, V, 1, p.periodic, p.force)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        R, U, V = oracle.run(p.mask, R, U, V, 1, p.periodic, p.force)
+    dt = time.perf_counter() - t0
+    value = size * rows * args.steps / dt / 1e6
+    sample = ("each step: one FP64 oracle step over the top %d rows (full "
+              "width %d) of the %d^2 lid-driven cavity" % (rows, size, size))
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 2),
+            "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": workload_config(size),
+            "cpu_baseline": {"value": round(value, 2), "unit": UNIT,
+                             "cores": oracle.max_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(value, 2), "unit": UNIT,
+                    "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def workload_config(size):
+    return {"workload": "D2Q9 LBMTau1 lid-driven cavity, lid u=0.1, FP32 "
+                        "storage, %dx%d nodes (largest point of the "
+                        "256^2-16384^2 single-domain sweep of the 1024^2 "
+                        "cavity configuration)" % (size, size),
+            "nx": size, "ny": size, "lid_u": 0.1, "storage": "f32",
+            "l2": "inputs larger than L2 (%.1f GB working set vs 129 MB L2)"
+                  % (BYTES_PER_LUP * size * size / 1e9),
+            "parallelism": "replicas"}
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        if backend == "nccl":
+            import torch
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    if args.impl == "reference":
+        rc = run_reference(args, rank, world)
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return rc
+
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1912_09327_gb300 import binding
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    n = args.size
+    dom, _ = cavity_domain(binding, n, stream)
+
+    for _ in range(max(args.warmup, 3)):
+        dom.step(1)
+    stream.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        per_step = time_steps(dom, stream, args.steps)
+        t1.record(stream)
+        stream.synchronize()
+    total_ms = t0.elapsed_time(t1)
+    torch.cuda.synchronize()
+    barrier(world)
+    total_ms = max_over_ranks(total_ms, world)
+    res, mass = dom.residual()
+    clocks = clk.summary()
+
+    nodes = n * n
+    value = nodes * args.steps * world / (total_ms * 1e3)
+    kernel_ms = statistics.mean(per_step)
+    peak, peak_src = load_peak()
+    achieved = BYTES_PER_LUP * nodes / (kernel_ms * 1e-3) / 1e9
+    traffic = load_traffic(nodes)
+    line = {"metric": METRIC, "value": round(value, 1), "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3),
+            "ms_per_step": round(total_ms / args.steps, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": workload_config(n),
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1),
+                         "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4),
+                         "traffic": traffic,
+                         "kernel": "lbm_step_kernel<reduce> + finalize "
+                                   "(events around lbm_step(ctx, 1))",
+                         "algorithmic_bytes_per_launch": BYTES_PER_LUP * nodes,
+                         "peak_source": peak_src},
+            "gpu_launches": 2 * args.steps,
+            "clocks": clocks,
+            "residual_last_step": res}
+
+    if rank == 0:
+        line["e2e"] = run_e2e(binding, dom, n, args.e2e_steps)
+    dom.close()
+    del dom
+    torch.cuda.empty_cache()
+    if rank == 0 and not args.no_sweep:
+        line["sweep"] = run_sweep(binding, stream,
+                                  [256, 512, 1024, 2048, 4096, 8192, 16384])
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(n)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

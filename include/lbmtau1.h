@@ -1,0 +1,174 @@
+/*
+ * lbmtau1.h - C ABI of the GB300 (sm_103a) LBMTau1 library.
+ *
+ * LBMTau1 is the D2Q9 lattice Boltzmann method with the relaxation time
+ * fixed at tau = 1 (Matyka & Dzikowski, arXiv:1912.09327).  With tau = 1 the
+ * post-collision populations are the equilibria, Eq. (LBMTau1), so a node's
+ * new density and momentum are the sums of the equilibria of its nine
+ * neighbours, Eqs. (rhotau1) and (utau1).  Only the moments are stored: two
+ * copies (ping-pong, Section 2.1) of density and x/y momentum, as in
+ * Eq. (LBMTau1memory).
+ *
+ * Conventions shared by every call:
+ *   - A domain is nx * ny nodes.  Host arrays are row-major, idx = y*nx + x.
+ *   - Node types (the flag array F of Algorithm 1, widened to three values):
+ *       LBM_FLUID  0  updated every step;
+ *       LBM_SOLID  1  no-slip wall, never updated; a fluid node pulling from
+ *                     it takes the zero-velocity equilibrium of its own
+ *                     density, w_k rho(x) (Eq. feqnoslip);
+ *       LBM_FIXED  2  fixed-equilibrium node (the moving lid of Section 3 and
+ *                     of Appendix A): never updated, pulled from like fluid.
+ *   - An axis flagged periodic wraps; on a non-periodic axis a neighbour
+ *     outside the domain counts as solid.
+ *   - The body force (fx, fy) is added to a neighbour's momentum before its
+ *     equilibrium is formed (Algorithm 1): u = (U + fx) / rho.
+ *   - Moments cross the ABI as density rho and momentum (jx, jy) = rho*u,
+ *     the quantities Eqs. (rhotau1) and (utau1) evolve, in double precision.
+ *     Device storage is FP32: rho - 1, jx, jy.
+ *   - Every call returns LBM_OK (0) or a negative status; nothing aborts or
+ *     throws across the ABI.  lbm_last_error() describes the last failure.
+ *   - All device work is enqueued on the CUDA stream given to lbm_create.
+ *     Calls that hand results to the host (lbm_moments, lbm_residual)
+ *     synchronise that stream.  A context is not thread-safe.
+ */
+#ifndef LBMTAU1_H
+#define LBMTAU1_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define LBM_OK 0
+#define LBM_E_INVAL (-1)     /* bad argument (null pointer, size, type) */
+#define LBM_E_WORKSPACE (-2) /* workspace missing, too small or misaligned */
+#define LBM_E_CUDA (-3)      /* a CUDA runtime call or launch failed */
+#define LBM_E_UNSTABLE (-4)  /* a step produced rho <= 0 or a non-finite value */
+#define LBM_E_STATE (-5)     /* call out of order (e.g. step before geometry) */
+
+/* Node types. */
+#define LBM_FLUID 0
+#define LBM_SOLID 1
+#define LBM_FIXED 2
+
+/* Device storage formats. */
+#define LBM_STORAGE_F32 0 /* rho - 1, jx, jy as float32 (24 B/node, 2 copies) */
+
+/* Problem statement.  Zero-initialise before filling in. */
+typedef struct lbm_params {
+  int64_t nx;         /* nodes along x, >= 1 */
+  int64_t ny;         /* nodes along y, >= 1 */
+  int32_t periodic_x; /* nonzero: x wraps (e.g. the channel of Section 3) */
+  int32_t periodic_y; /* nonzero: y wraps */
+  double fx;          /* body force, momentum added per node per step */
+  double fy;
+  int32_t storage;    /* LBM_STORAGE_F32 */
+  int32_t reserved;   /* must be 0 */
+} lbm_params;
+
+typedef struct lbm_ctx lbm_ctx;
+
+/*
+ * Device workspace needed for a domain, in bytes; 0 when p is invalid.
+ * The workspace holds both copies of the three moment fields (rows padded to
+ * a multiple of 32 nodes), the node-type array, per-block reduction partials
+ * and a bounded staging buffer for host transfers.
+ */
+size_t lbm_workspace_bytes(const lbm_params *p);
+
+/*
+ * Creates a context over a caller-owned device workspace.
+ *   p               problem statement (copied).
+ *   dev_workspace   device pointer, 256-byte aligned, >= lbm_workspace_bytes(p)
+ *                   bytes; owned by the caller and must outlive the context.
+ *   workspace_bytes size of that allocation.
+ *   cuda_stream     cudaStream_t to enqueue all work on (NULL = legacy stream).
+ *   out             receives the context.
+ * The fields start at rest (rho = 1, j = 0) with every node fluid; call
+ * lbm_set_geometry before stepping.
+ * Errors: LBM_E_INVAL, LBM_E_WORKSPACE.
+ */
+int lbm_create(const lbm_params *p, void *dev_workspace, size_t workspace_bytes,
+               void *cuda_stream, lbm_ctx **out);
+
+/*
+ * Sets the node types from a host array of nx*ny bytes (values 0, 1, 2; see
+ * above; Algorithm 1, first line) and resets both copies of the fields to
+ * rest, rho = 1 and j = 0 (the initial state of Section 2.1).  The array is
+ * copied; the caller keeps ownership.
+ * Errors: LBM_E_INVAL (null or a value > 2), LBM_E_CUDA.
+ */
+int lbm_set_geometry(lbm_ctx *ctx, const uint8_t *host_mask);
+
+/*
+ * Loads a state: host arrays of nx*ny doubles with density rho (> 0) and
+ * momentum jx, jy.  Fixed nodes keep the values given here for every later
+ * step (a lid with speed u0 is rho = 1, jx = u0, jy = 0 as in Appendix A).
+ * Errors: LBM_E_INVAL, LBM_E_STATE (no geometry yet), LBM_E_CUDA.
+ */
+int lbm_set_moments(lbm_ctx *ctx, const double *rho, const double *jx,
+                    const double *jy);
+
+/*
+ * Enqueues nsteps LBMTau1 time steps (Algorithm 1), asynchronously.  The last
+ * step of the call also reduces the residual and mass that lbm_residual
+ * returns and checks for rho <= 0 or non-finite values.  nsteps = 0 is a
+ * no-op.
+ * Errors: LBM_E_INVAL (nsteps < 0), LBM_E_STATE, LBM_E_CUDA (launch failure).
+ */
+int lbm_step(lbm_ctx *ctx, int64_t nsteps);
+
+/*
+ * Copies the current state to caller-owned host arrays of nx*ny doubles:
+ * density, and momentum jx, jy (velocity = j / rho).  Solid and fixed nodes
+ * return the values they hold.  Synchronises the stream.
+ * Errors: LBM_E_INVAL, LBM_E_STATE, LBM_E_CUDA.
+ */
+int lbm_moments(lbm_ctx *ctx, double *rho, double *jx, double *jy);
+
+/*
+ * Exact state transfer in the device storage format, for checkpoint/resume:
+ * three caller-owned host arrays of nx*ny elements (float for
+ * LBM_STORAGE_F32) holding rho - 1, jx and jy exactly as stored.  A state
+ * saved with lbm_get_state and loaded with lbm_set_state into a context with
+ * the same parameters and geometry continues bit for bit.  lbm_get_state
+ * synchronises; lbm_set_state returns once the host arrays have been read.
+ * Errors: LBM_E_INVAL, LBM_E_STATE (no geometry yet), LBM_E_CUDA.
+ */
+int lbm_get_state(lbm_ctx *ctx, void *drho, void *jx, void *jy);
+int lbm_set_state(lbm_ctx *ctx, const void *drho, const void *jx,
+                  const void *jy);
+
+/*
+ * Residual and mass of the last step run by lbm_step, over fluid nodes, with
+ * velocity u = j / rho:
+ *   residual = sqrt(sum |u_n - u_{n-1}|^2 / sum |u_n|^2)  (the relative
+ *              velocity change between consecutive steps used as the
+ *              steady-state test in Section 3, taken over the whole field;
+ *              sqrt(sum |u_n - u_{n-1}|^2) when the flow is at rest),
+ *   mass     = sum rho_n.
+ * Either pointer may be NULL.  Sums are taken in FP64.  Synchronises.
+ * Errors: LBM_E_STATE (no step since the state was set), LBM_E_UNSTABLE
+ * (the last reduced step saw rho <= 0 or a non-finite value; the values are
+ * still written), LBM_E_CUDA.
+ */
+int lbm_residual(lbm_ctx *ctx, double *residual, double *mass);
+
+/* Frees the context's host state; the workspace stays the caller's. */
+void lbm_destroy(lbm_ctx *ctx);
+
+/* Message for the last failed call on ctx ("" when none; static text for a
+ * NULL ctx).  Valid until the next call on ctx. */
+const char *lbm_last_error(const lbm_ctx *ctx);
+
+/* Static name of a status code. */
+const char *lbm_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBMTAU1_H */

@@ -1,0 +1,235 @@
+"""Thin ctypes binding of the C ABI declared in ``include/lbmtau1.h``.
+
+The functions keep the C names and only marshal arguments; every step of the
+LBMTau1 path runs in the sm_103a kernels of ``liblbmtau1.so``.  PyTorch is
+used by ``Domain`` for the device workspace and the CUDA stream only.
+Importing this module raises if the library has not been built: there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+LBM_OK = 0
+LBM_E_INVAL = -1
+LBM_E_WORKSPACE = -2
+LBM_E_CUDA = -3
+LBM_E_UNSTABLE = -4
+LBM_E_STATE = -5
+LBM_FLUID, LBM_SOLID, LBM_FIXED = 0, 1, 2
+LBM_STORAGE_F32 = 0
+
+LIB_PATH = _build.LIB
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        "liblbmtau1.so is not built (run __graft_entry__.build()); the LBMTau1 "
+        "path has no CPU fallback")
+_lib = ctypes.CDLL(LIB_PATH)
+
+
+class lbm_params(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int64), ("ny", ctypes.c_int64),
+                ("periodic_x", ctypes.c_int32), ("periodic_y", ctypes.c_int32),
+                ("fx", ctypes.c_double), ("fy", ctypes.c_double),
+                ("storage", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+_P = ctypes.POINTER(lbm_params)
+_vp = ctypes.c_void_p
+_lib.lbm_workspace_bytes.argtypes = [_P]
+_lib.lbm_workspace_bytes.restype = ctypes.c_size_t
+_lib.lbm_create.argtypes = [_P, _vp, ctypes.c_size_t, _vp,
+                            ctypes.POINTER(_vp)]
+_lib.lbm_create.restype = ctypes.c_int
+_lib.lbm_set_geometry.argtypes = [_vp, _vp]
+_lib.lbm_set_geometry.restype = ctypes.c_int
+_lib.lbm_set_moments.argtypes = [_vp, _vp, _vp, _vp]
+_lib.lbm_set_moments.restype = ctypes.c_int
+_lib.lbm_step.argtypes = [_vp, ctypes.c_int64]
+_lib.lbm_step.restype = ctypes.c_int
+_lib.lbm_moments.argtypes = [_vp, _vp, _vp, _vp]
+_lib.lbm_moments.restype = ctypes.c_int
+_lib.lbm_get_state.argtypes = [_vp, _vp, _vp, _vp]
+_lib.lbm_get_state.restype = ctypes.c_int
+_lib.lbm_set_state.argtypes = [_vp, _vp, _vp, _vp]
+_lib.lbm_set_state.restype = ctypes.c_int
+_lib.lbm_residual.argtypes = [_vp, ctypes.POINTER(ctypes.c_double),
+                              ctypes.POINTER(ctypes.c_double)]
+_lib.lbm_residual.restype = ctypes.c_int
+_lib.lbm_destroy.argtypes = [_vp]
+_lib.lbm_destroy.restype = None
+_lib.lbm_last_error.argtypes = [_vp]
+_lib.lbm_last_error.restype = ctypes.c_char_p
+_lib.lbm_status_string.argtypes = [ctypes.c_int]
+_lib.lbm_status_string.restype = ctypes.c_char_p
+
+
+class LbmError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("%s: %s" % (lbm_status_string(status), message))
+        self.status = status
+
+
+def lbm_status_string(status: int) -> str:
+    return _lib.lbm_status_string(int(status)).decode()
+
+
+def lbm_last_error(ctx) -> str:
+    return _lib.lbm_last_error(ctx).decode()
+
+
+def _check(status, ctx=None):
+    if status != LBM_OK:
+        raise LbmError(status, lbm_last_error(ctx) if ctx else "")
+    return status
+
+
+def make_params(nx, ny, periodic=(False, False), force=(0.0, 0.0),
+                storage=LBM_STORAGE_F32) -> lbm_params:
+    return lbm_params(int(nx), int(ny), int(bool(periodic[0])),
+                      int(bool(periodic[1])), float(force[0]), float(force[1]),
+                      int(storage), 0)
+
+
+def _ptr(a):
+    """Address of a host buffer: a C-contiguous numpy array or CPU tensor."""
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous:
+            raise ValueError("host arrays must be C-contiguous")
+        return a.ctypes.data
+    return int(a.data_ptr())
+
+
+def lbm_workspace_bytes(params: lbm_params) -> int:
+    return int(_lib.lbm_workspace_bytes(ctypes.byref(params)))
+
+
+def lbm_create(params: lbm_params, dev_workspace: int, workspace_bytes: int,
+               cuda_stream: int = 0):
+    ctx = _vp()
+    _check(_lib.lbm_create(ctypes.byref(params), _vp(dev_workspace),
+                           workspace_bytes, _vp(cuda_stream),
+                           ctypes.byref(ctx)))
+    return ctx
+
+
+def lbm_set_geometry(ctx, host_mask) -> None:
+    if isinstance(host_mask, np.ndarray):
+        host_mask = np.ascontiguousarray(host_mask, dtype=np.uint8)
+    _check(_lib.lbm_set_geometry(ctx, _vp(_ptr(host_mask))), ctx)
+
+
+def lbm_set_moments(ctx, rho, jx, jy) -> None:
+    """Host density and momentum (float64, nx*ny each)."""
+    arrs = [np.ascontiguousarray(a, dtype=np.float64)
+            if isinstance(a, np.ndarray) else a for a in (rho, jx, jy)]
+    _check(_lib.lbm_set_moments(ctx, *[_vp(_ptr(a)) for a in arrs]), ctx)
+
+
+def lbm_step(ctx, nsteps: int) -> None:
+    _check(_lib.lbm_step(ctx, int(nsteps)), ctx)
+
+
+def lbm_moments(ctx, rho, jx, jy) -> None:
+    """Fills caller-owned host float64 buffers (numpy or pinned tensors)."""
+    for a in (rho, jx, jy):
+        if isinstance(a, np.ndarray) and a.dtype != np.float64:
+            raise TypeError("moment buffers must be float64")
+    _check(_lib.lbm_moments(ctx, *[_vp(_ptr(a)) for a in (rho, jx, jy)]), ctx)
+
+
+def lbm_get_state(ctx, drho, jx, jy) -> None:
+    """Fills host float32 buffers with the stored rho - 1, jx, jy."""
+    for a in (drho, jx, jy):
+        if isinstance(a, np.ndarray) and a.dtype != np.float32:
+            raise TypeError("state buffers must be float32")
+    _check(_lib.lbm_get_state(ctx, *[_vp(_ptr(a)) for a in (drho, jx, jy)]), ctx)
+
+
+def lbm_set_state(ctx, drho, jx, jy) -> None:
+    """Loads host float32 rho - 1, jx, jy exactly."""
+    arrs = [np.ascontiguousarray(a, dtype=np.float32)
+            if isinstance(a, np.ndarray) else a for a in (drho, jx, jy)]
+    _check(_lib.lbm_set_state(ctx, *[_vp(_ptr(a)) for a in arrs]), ctx)
+
+
+def lbm_residual(ctx):
+    """(residual, mass) of the last step; raises LbmError(LBM_E_UNSTABLE)."""
+    r = ctypes.c_double(); m = ctypes.c_double()
+    st = _lib.lbm_residual(ctx, ctypes.byref(r), ctypes.byref(m))
+    _check(st, ctx)
+    return r.value, m.value
+
+
+def lbm_destroy(ctx) -> None:
+    _lib.lbm_destroy(ctx)
+
+
+class Domain:
+    """One LBMTau1 domain on a GPU: a torch-allocated workspace, a stream and
+    a context.  Methods map one-to-one to the C calls."""
+
+    def __init__(self, nx, ny, periodic=(False, False), force=(0.0, 0.0),
+                 device="cuda", stream=None):
+        import torch
+        self.nx, self.ny = int(nx), int(ny)
+        self.params = make_params(nx, ny, periodic, force)
+        nbytes = lbm_workspace_bytes(self.params)
+        if nbytes == 0:
+            raise LbmError(LBM_E_INVAL, "invalid domain parameters")
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.ctx = lbm_create(self.params, self.workspace.data_ptr(), nbytes,
+                              self.stream.cuda_stream)
+
+    @classmethod
+    def from_problem(cls, prob, **kw):
+        ny, nx = prob.mask.shape
+        d = cls(nx, ny, prob.periodic, prob.force, **kw)
+        d.set_geometry(prob.mask)
+        d.set_moments(prob.rho, prob.jx, prob.jy)
+        return d
+
+    def set_geometry(self, mask):
+        lbm_set_geometry(self.ctx, mask)
+
+    def set_moments(self, rho, jx, jy):
+        lbm_set_moments(self.ctx, rho, jx, jy)
+
+    def step(self, nsteps=1):
+        lbm_step(self.ctx, nsteps)
+
+    def moments(self, out=None):
+        if out is None:
+            out = tuple(np.empty((self.ny, self.nx), np.float64) for _ in range(3))
+        lbm_moments(self.ctx, *out)
+        return out
+
+    def get_state(self, out=None):
+        if out is None:
+            out = tuple(np.empty((self.ny, self.nx), np.float32) for _ in range(3))
+        lbm_get_state(self.ctx, *out)
+        return out
+
+    def set_state(self, drho, jx, jy):
+        lbm_set_state(self.ctx, drho, jx, jy)
+
+    def residual(self):
+        return lbm_residual(self.ctx)
+
+    def close(self):
+        if self.ctx:
+            lbm_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,390 @@
+// C ABI of the LBMTau1 library: context, workspace layout, host transfers and
+// the time loop (Algorithm 1 of arXiv:1912.09327, repeated with the two grid
+// copies of Section 2.1 swapped after every step).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+
+#include "../../include/lbmtau1.h"
+#include "lbm_step.cuh"
+
+using lbmtau1::Fields;
+
+namespace {
+
+constexpr int64_t kPitchAlign = 32;           // nodes; rows start 128-B aligned
+constexpr size_t kAlign = 256;                // bytes; every workspace region
+constexpr int64_t kStagingNodes = 1 << 20;    // host-transfer chunk (nodes)
+constexpr int64_t kMaxExtent = int64_t(1) << 31;
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+struct Layout {
+  int64_t pitch = 0, staging_rows = 0, nblocks = 0;
+  size_t field_bytes = 0;   // one field plane
+  size_t off_fields = 0;    // 6 planes: copy 0 (d, jx, jy), copy 1 (d, jx, jy)
+  size_t off_mask = 0;
+  size_t off_partials = 0;
+  size_t off_result = 0;    // 3 doubles + flag
+  size_t off_staging = 0;
+  size_t total = 0;
+};
+
+bool params_ok(const lbm_params *p) {
+  return p && p->nx >= 1 && p->ny >= 1 && p->nx <= kMaxExtent &&
+         p->ny <= kMaxExtent && p->storage == LBM_STORAGE_F32 &&
+         p->reserved == 0 && isfinite(p->fx) && isfinite(p->fy);
+}
+
+Layout make_layout(const lbm_params *p) {
+  Layout L;
+  L.pitch = (p->nx + kPitchAlign - 1) / kPitchAlign * kPitchAlign;
+  const size_t plane = static_cast<size_t>(L.pitch) * p->ny;
+  L.field_bytes = align_up(plane * sizeof(float), kAlign);
+  L.nblocks = lbmtau1::step_blocks(p->nx, p->ny);
+  int64_t rows = kStagingNodes / p->nx;
+  if (rows < 1) rows = 1;
+  if (rows > p->ny) rows = p->ny;
+  L.staging_rows = rows;
+  size_t off = 0;
+  L.off_fields = off;
+  off += 6 * L.field_bytes;
+  L.off_mask = off;
+  off += align_up(plane, kAlign);
+  L.off_partials = off;
+  off += align_up(static_cast<size_t>(L.nblocks) * 3 * sizeof(double), kAlign);
+  L.off_result = off;
+  off += kAlign;
+  L.off_staging = off;
+  off += align_up(static_cast<size_t>(rows) * p->nx * 3 * sizeof(double),
+                  kAlign);
+  L.total = off;
+  return L;
+}
+
+}  // namespace
+
+struct lbm_ctx {
+  lbm_params p;
+  Layout L;
+  char *base;
+  Fields f[2];
+  uint8_t *mask;
+  double *partials;
+  double *result;       // sum |du|^2, sum |u|^2, sum (rho - 1)
+  unsigned *flag;       // follows the three doubles
+  double *staging;
+  cudaStream_t stream;
+  int cur;              // copy holding the current state
+  bool has_geometry;
+  bool has_residual;
+  int64_t n_fluid;
+  char err[256];
+};
+
+namespace {
+
+int fail(lbm_ctx *c, int status, const char *fmt, ...) {
+  if (c) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(c->err, sizeof c->err, fmt, ap);
+    va_end(ap);
+  }
+  return status;
+}
+
+int cuda_fail(lbm_ctx *c, cudaError_t e, const char *what) {
+  return fail(c, LBM_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// Makes the workspace's device current (callers may run several GPUs).
+int bind_device(lbm_ctx *c) {
+  cudaPointerAttributes attr;
+  cudaError_t e = cudaPointerGetAttributes(&attr, c->base);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaPointerGetAttributes");
+  if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged)
+    return fail(c, LBM_E_WORKSPACE, "workspace is not device memory");
+  int cur = -1;
+  e = cudaGetDevice(&cur);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaGetDevice");
+  if (cur != attr.device) {
+    e = cudaSetDevice(attr.device);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+  }
+  return LBM_OK;
+}
+
+int reset_flags(lbm_ctx *c) {
+  cudaError_t e = cudaMemsetAsync(c->result, 0, kAlign, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemsetAsync(result)");
+  c->has_residual = false;
+  return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t lbm_workspace_bytes(const lbm_params *p) {
+  if (!params_ok(p)) return 0;
+  return make_layout(p).total;
+}
+
+int lbm_create(const lbm_params *p, void *dev_workspace, size_t workspace_bytes,
+               void *cuda_stream, lbm_ctx **out) {
+  if (!out) return LBM_E_INVAL;
+  *out = nullptr;
+  if (!params_ok(p)) return LBM_E_INVAL;
+  const Layout L = make_layout(p);
+  if (!dev_workspace || reinterpret_cast<uintptr_t>(dev_workspace) % kAlign ||
+      workspace_bytes < L.total)
+    return LBM_E_WORKSPACE;
+  lbm_ctx *c = new (std::nothrow) lbm_ctx();
+  if (!c) return LBM_E_INVAL;
+  c->p = *p;
+  c->L = L;
+  c->base = static_cast<char *>(dev_workspace);
+  for (int k = 0; k < 2; ++k) {
+    char *q = c->base + L.off_fields + 3 * k * L.field_bytes;
+    c->f[k].d = reinterpret_cast<float *>(q);
+    c->f[k].jx = reinterpret_cast<float *>(q + L.field_bytes);
+    c->f[k].jy = reinterpret_cast<float *>(q + 2 * L.field_bytes);
+  }
+  c->mask = reinterpret_cast<uint8_t *>(c->base + L.off_mask);
+  c->partials = reinterpret_cast<double *>(c->base + L.off_partials);
+  c->result = reinterpret_cast<double *>(c->base + L.off_result);
+  c->flag = reinterpret_cast<unsigned *>(c->result + 3);
+  c->staging = reinterpret_cast<double *>(c->base + L.off_staging);
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  c->cur = 0;
+  c->has_geometry = false;
+  c->has_residual = false;
+  c->n_fluid = 0;
+  c->err[0] = '\0';
+  *out = c;
+  return LBM_OK;
+}
+
+int lbm_set_geometry(lbm_ctx *c, const uint8_t *host_mask) {
+  if (!c) return LBM_E_INVAL;
+  if (!host_mask) return fail(c, LBM_E_INVAL, "host_mask is NULL");
+  const int64_t n = c->p.nx * c->p.ny;
+  int64_t fluid = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    if (host_mask[i] > LBM_FIXED)
+      return fail(c, LBM_E_INVAL, "node %lld has type %d (allowed 0, 1, 2)",
+                  static_cast<long long>(i), host_mask[i]);
+    fluid += host_mask[i] == LBM_FLUID;
+  }
+  int st = bind_device(c);
+  if (st) return st;
+  const size_t plane = static_cast<size_t>(c->L.pitch) * c->p.ny;
+  cudaError_t e = cudaMemsetAsync(c->mask, LBM_SOLID, plane, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemsetAsync(mask)");
+  e = cudaMemcpy2DAsync(c->mask, c->L.pitch, host_mask, c->p.nx, c->p.nx,
+                        c->p.ny, cudaMemcpyHostToDevice, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpy2DAsync(mask)");
+  // rest state rho = 1 (delta = 0), j = 0 in both copies
+  e = cudaMemsetAsync(c->base + c->L.off_fields, 0, 6 * c->L.field_bytes,
+                      c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemsetAsync(fields)");
+  st = reset_flags(c);
+  if (st) return st;
+  // the host mask may be released as soon as this call returns
+  e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamSynchronize");
+  c->cur = 0;
+  c->n_fluid = fluid;
+  c->has_geometry = true;
+  c->err[0] = '\0';
+  return LBM_OK;
+}
+
+int lbm_set_moments(lbm_ctx *c, const double *rho, const double *jx,
+                    const double *jy) {
+  if (!c) return LBM_E_INVAL;
+  if (!rho || !jx || !jy) return fail(c, LBM_E_INVAL, "null moment array");
+  if (!c->has_geometry)
+    return fail(c, LBM_E_STATE, "lbm_set_geometry has not been called");
+  int st = bind_device(c);
+  if (st) return st;
+  const int64_t nx = c->p.nx;
+  for (int64_t y0 = 0; y0 < c->p.ny; y0 += c->L.staging_rows) {
+    const int64_t rows =
+        y0 + c->L.staging_rows <= c->p.ny ? c->L.staging_rows : c->p.ny - y0;
+    const size_t n = static_cast<size_t>(rows) * nx;
+    const double *src[3] = {rho, jx, jy};
+    for (int k = 0; k < 3; ++k) {
+      cudaError_t e = cudaMemcpyAsync(c->staging + k * n, src[k] + y0 * nx,
+                                      n * sizeof(double),
+                                      cudaMemcpyHostToDevice, c->stream);
+      if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpyAsync(H2D)");
+    }
+    cudaError_t e = lbmtau1::launch_pack(c->staging, c->f[c->cur], nx,
+                                         c->L.pitch, y0, rows, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "pack kernel");
+  }
+  st = reset_flags(c);
+  if (st) return st;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamSynchronize");
+  c->err[0] = '\0';
+  return LBM_OK;
+}
+
+int lbm_set_state(lbm_ctx *c, const void *drho, const void *jx,
+                  const void *jy) {
+  if (!c) return LBM_E_INVAL;
+  if (!drho || !jx || !jy) return fail(c, LBM_E_INVAL, "null state array");
+  if (!c->has_geometry)
+    return fail(c, LBM_E_STATE, "lbm_set_geometry has not been called");
+  int st = bind_device(c);
+  if (st) return st;
+  const void *src[3] = {drho, jx, jy};
+  float *dst[3] = {c->f[c->cur].d, c->f[c->cur].jx, c->f[c->cur].jy};
+  const size_t row = static_cast<size_t>(c->p.nx) * sizeof(float);
+  for (int k = 0; k < 3; ++k) {
+    cudaError_t e = cudaMemcpy2DAsync(dst[k], c->L.pitch * sizeof(float),
+                                      src[k], row, row, c->p.ny,
+                                      cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpy2DAsync(H2D)");
+  }
+  st = reset_flags(c);
+  if (st) return st;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamSynchronize");
+  c->err[0] = '\0';
+  return LBM_OK;
+}
+
+int lbm_get_state(lbm_ctx *c, void *drho, void *jx, void *jy) {
+  if (!c) return LBM_E_INVAL;
+  if (!drho || !jx || !jy) return fail(c, LBM_E_INVAL, "null state array");
+  if (!c->has_geometry)
+    return fail(c, LBM_E_STATE, "lbm_set_geometry has not been called");
+  int st = bind_device(c);
+  if (st) return st;
+  void *dst[3] = {drho, jx, jy};
+  const float *src[3] = {c->f[c->cur].d, c->f[c->cur].jx, c->f[c->cur].jy};
+  const size_t row = static_cast<size_t>(c->p.nx) * sizeof(float);
+  for (int k = 0; k < 3; ++k) {
+    cudaError_t e = cudaMemcpy2DAsync(dst[k], row, src[k],
+                                      c->L.pitch * sizeof(float), row,
+                                      c->p.ny, cudaMemcpyDeviceToHost,
+                                      c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpy2DAsync(D2H)");
+  }
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamSynchronize");
+  c->err[0] = '\0';
+  return LBM_OK;
+}
+
+int lbm_step(lbm_ctx *c, int64_t nsteps) {
+  if (!c) return LBM_E_INVAL;
+  if (nsteps < 0) return fail(c, LBM_E_INVAL, "nsteps < 0");
+  if (!c->has_geometry)
+    return fail(c, LBM_E_STATE, "lbm_set_geometry has not been called");
+  if (nsteps == 0) return LBM_OK;
+  lbmtau1::StepLaunch a;
+  a.mask = c->mask;
+  a.nx = c->p.nx;
+  a.ny = c->p.ny;
+  a.pitch = c->L.pitch;
+  a.periodic_x = c->p.periodic_x != 0;
+  a.periodic_y = c->p.periodic_y != 0;
+  a.fx = static_cast<float>(c->p.fx);
+  a.fy = static_cast<float>(c->p.fy);
+  a.partials = c->partials;
+  a.flag = c->flag;
+  for (int64_t s = 0; s < nsteps; ++s) {
+    a.src = c->f[c->cur];
+    a.dst = c->f[1 - c->cur];
+    cudaError_t e = lbmtau1::launch_step(a, s == nsteps - 1, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "step kernel launch");
+    c->cur = 1 - c->cur;
+  }
+  cudaError_t e = lbmtau1::launch_finalize(c->partials, c->L.nblocks,
+                                           c->result, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "finalize kernel launch");
+  c->has_residual = true;
+  return LBM_OK;
+}
+
+int lbm_moments(lbm_ctx *c, double *rho, double *jx, double *jy) {
+  if (!c) return LBM_E_INVAL;
+  if (!rho || !jx || !jy) return fail(c, LBM_E_INVAL, "null moment array");
+  if (!c->has_geometry)
+    return fail(c, LBM_E_STATE, "lbm_set_geometry has not been called");
+  int st = bind_device(c);
+  if (st) return st;
+  const int64_t nx = c->p.nx;
+  for (int64_t y0 = 0; y0 < c->p.ny; y0 += c->L.staging_rows) {
+    const int64_t rows =
+        y0 + c->L.staging_rows <= c->p.ny ? c->L.staging_rows : c->p.ny - y0;
+    const size_t n = static_cast<size_t>(rows) * nx;
+    cudaError_t e = lbmtau1::launch_unpack(c->f[c->cur], c->staging, nx,
+                                           c->L.pitch, y0, rows, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "unpack kernel");
+    double *dst[3] = {rho, jx, jy};
+    for (int k = 0; k < 3; ++k) {
+      e = cudaMemcpyAsync(dst[k] + y0 * nx, c->staging + k * n,
+                          n * sizeof(double), cudaMemcpyDeviceToHost,
+                          c->stream);
+      if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpyAsync(D2H)");
+    }
+  }
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamSynchronize");
+  c->err[0] = '\0';
+  return LBM_OK;
+}
+
+int lbm_residual(lbm_ctx *c, double *residual, double *mass) {
+  if (!c) return LBM_E_INVAL;
+  if (!c->has_residual)
+    return fail(c, LBM_E_STATE, "no step has run since the state was set");
+  int st = bind_device(c);
+  if (st) return st;
+  double h[4];
+  cudaError_t e = cudaMemcpyAsync(h, c->result, sizeof h,
+                                  cudaMemcpyDeviceToHost, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpyAsync(result)");
+  e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamSynchronize");
+  unsigned flag;
+  memcpy(&flag, &h[3], sizeof flag);
+  const double num = h[0], den = h[1];
+  if (residual) *residual = den > 0.0 ? sqrt(num / den) : sqrt(num);
+  if (mass) *mass = static_cast<double>(c->n_fluid) + h[2];
+  if (flag)
+    return fail(c, LBM_E_UNSTABLE,
+                "a step produced rho <= 0 or a non-finite moment");
+  c->err[0] = '\0';
+  return LBM_OK;
+}
+
+void lbm_destroy(lbm_ctx *c) { delete c; }
+
+const char *lbm_last_error(const lbm_ctx *c) {
+  return c ? c->err : "null context";
+}
+
+const char *lbm_status_string(int status) {
+  switch (status) {
+    case LBM_OK: return "LBM_OK";
+    case LBM_E_INVAL: return "LBM_E_INVAL";
+    case LBM_E_WORKSPACE: return "LBM_E_WORKSPACE";
+    case LBM_E_CUDA: return "LBM_E_CUDA";
+    case LBM_E_UNSTABLE: return "LBM_E_UNSTABLE";
+    case LBM_E_STATE: return "LBM_E_STATE";
+    default: return "LBM_E_UNKNOWN";
+  }
+}
+
+}  // extern "C"

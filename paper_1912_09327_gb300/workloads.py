@@ -88,7 +88,9 @@ def porous(n: int = 4096, seed: int = 0, r_min: int = 8, r_max: int = 24,
     mask = np.zeros((ny, nx), np.uint8)
     cx = np.empty(0); cy = np.empty(0); cr = np.empty(0)
     tries = 0
-    while mask.mean() < solid_fraction and tries < max_tries:
+    solid = 0                      # discs never share nodes (gap of one node)
+    target = solid_fraction * nx * ny
+    while solid < target and tries < max_tries:
         tries += 1
         r = int(rng.integers(r_min, r_max + 1))
         x0 = rng.uniform(0, nx); y0 = rng.uniform(0, ny)
@@ -103,6 +105,7 @@ def porous(n: int = 4096, seed: int = 0, r_min: int = 8, r_max: int = 24,
         X, Y = np.meshgrid(xs, ys)
         inside = (X - x0) ** 2 + (Y - y0) ** 2 <= r * r
         mask[Y[inside] % ny, X[inside] % nx] = SOLID
+        solid += int(inside.sum())
     rr, u, v = _rest_state(mask.shape)
     return Problem("porous", mask, (True, True), (fx, 0.0), rr, u, v,
                    {"discs": int(cx.size), "solid_fraction": float(mask.mean()),

@@ -1,0 +1,118 @@
+"""Host-side checks of the C ABI library (no GPU needed): it loads, exports
+every function include/lbmtau1.h declares, sizes its workspace after the
+paper's storage model, and validates arguments before any CUDA call."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "lbmtau1.h")
+
+
+@pytest.fixture(scope="module")
+def b():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1912_09327_gb300 import binding
+    return binding
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbm_\w+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(b):
+    names = declared_functions()
+    assert len(names) >= 12
+    lib = ctypes.CDLL(b.LIB_PATH)
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_workspace_follows_storage_model(b):
+    """Eq. (LBMTau1memory): 2 N_f c = 24 bytes per node for the two copies of
+    (rho, u_x, u_y) in FP32, against (2Q + N_f) c = 84 for the standard
+    algorithm (Eq. lbmmemory); golden values from Section 4."""
+    gold = {}
+    for line in open(os.path.join(ROOT, "tests", "golden", "memory_model.txt")):
+        if line.strip() and not line.startswith("#"):
+            k, v = line.split()
+            gold[k] = int(v)
+    Q, Nf, c = gold["Q"], gold["N_f"], gold["bytes_per_number_float"]
+    assert 2 * Nf * c == gold["lbmtau1_bytes_per_node"]
+    assert (2 * Q + Nf) * c == gold["standard_lbm_bytes_per_node"]
+    # large domain: fields (24 B) + node type (1 B) + bounded extras
+    n = 16384
+    ws = b.lbm_workspace_bytes(b.make_params(n, n))
+    per_node = ws / (n * n)
+    assert gold["lbmtau1_bytes_per_node"] + 1 <= per_node < 25.2
+    # the paper's 1000 x 1000 example: 24 MB of fields (rows padded to 1024)
+    ws1000 = b.lbm_workspace_bytes(b.make_params(1000, 1000))
+    fields = 6 * 4 * 1024 * 1000
+    assert fields / 1e6 == pytest.approx(gold["cavity_1000_lbmtau1_MB"], rel=0.03)
+    assert ws1000 >= fields + 1024 * 1000
+
+
+@pytest.mark.parametrize("bad", [dict(nx=0), dict(ny=0), dict(nx=-3),
+                                 dict(storage=7), dict(reserved=1),
+                                 dict(fx=float("nan"))])
+def test_invalid_params(b, bad):
+    p = b.make_params(10, 10)
+    for k, v in bad.items():
+        setattr(p, k, v)
+    assert b.lbm_workspace_bytes(p) == 0
+    ctx = ctypes.c_void_p()
+    st = b._lib.lbm_create(ctypes.byref(p), ctypes.c_void_p(1 << 20), 1 << 40,
+                           None, ctypes.byref(ctx))
+    assert st == b.LBM_E_INVAL and not ctx.value
+
+
+def test_create_validates_workspace(b):
+    p = b.make_params(100, 50)
+    need = b.lbm_workspace_bytes(p)
+    ctx = ctypes.c_void_p()
+    create = b._lib.lbm_create
+    assert create(ctypes.byref(p), None, need, None, ctypes.byref(ctx)) == b.LBM_E_WORKSPACE
+    assert create(ctypes.byref(p), ctypes.c_void_p(4096 + 8), need, None,
+                  ctypes.byref(ctx)) == b.LBM_E_WORKSPACE
+    assert create(ctypes.byref(p), ctypes.c_void_p(4096), need - 1, None,
+                  ctypes.byref(ctx)) == b.LBM_E_WORKSPACE
+    assert create(ctypes.byref(p), ctypes.c_void_p(4096), need, None, None) == b.LBM_E_INVAL
+
+
+def test_call_order_and_arguments_checked_on_host(b):
+    """A context over a never-dereferenced aligned address: every call below
+    fails its host-side checks before touching the device."""
+    p = b.make_params(20, 10, (True, False), (1e-5, 0))
+    ctx = b.lbm_create(p, 1 << 20, b.lbm_workspace_bytes(p))
+    try:
+        lib = b._lib
+        assert lib.lbm_step(ctx, 5) == b.LBM_E_STATE
+        assert "geometry" in b.lbm_last_error(ctx)
+        assert lib.lbm_step(ctx, -1) == b.LBM_E_INVAL
+        assert lib.lbm_residual(ctx, None, None) == b.LBM_E_STATE
+        assert lib.lbm_moments(ctx, None, None, None) == b.LBM_E_INVAL
+        assert lib.lbm_get_state(ctx, None, None, None) == b.LBM_E_INVAL
+        assert lib.lbm_set_geometry(ctx, None) == b.LBM_E_INVAL
+        bad = np.zeros((10, 20), np.uint8)
+        bad[3, 4] = 3
+        assert lib.lbm_set_geometry(ctx, bad.ctypes.data) == b.LBM_E_INVAL
+        assert "type 3" in b.lbm_last_error(ctx)
+        z = np.zeros(200)
+        assert lib.lbm_set_moments(ctx, z.ctypes.data, z.ctypes.data,
+                                   z.ctypes.data) == b.LBM_E_STATE
+    finally:
+        b.lbm_destroy(ctx)
+    assert b.lbm_last_error(None) == "null context"
+
+
+def test_status_strings(b):
+    for name in ["LBM_OK", "LBM_E_INVAL", "LBM_E_WORKSPACE", "LBM_E_CUDA",
+                 "LBM_E_UNSTABLE", "LBM_E_STATE"]:
+        assert b.lbm_status_string(getattr(b, name)) == name
+    assert b.lbm_status_string(-99) == "LBM_E_UNKNOWN"

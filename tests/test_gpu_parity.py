@@ -1,0 +1,306 @@
+"""Parity of the sm_103a LBMTau1 kernels (through the C ABI) with the FP64
+CPU oracle, element by element on the same seeded inputs.
+
+Tolerances.  The device stores rho - 1 and j in FP32 and computes in FP32.
+- The channel case uses the bound the method is held to:
+  max|u_gpu - u_oracle| / max|u_oracle| <= 1e-5 after the full run.
+- General cases compare rho, jx, jy absolutely.  One step rounds each stored
+  value once (half an ulp, 6e-8 relative) plus the rounding of the increment,
+  which is a sum of O(10) terms of size <= |j| + |rho - 1| + 3|j|^2, so the
+  per-step error is a few 1e-8 times the field amplitude; errors do not grow
+  faster than linearly in the number of steps for these stable flows.  With
+  amplitude a and n steps the tests allow 4e-7 * max(a, 1e-3) * n + 1e-9.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1912_09327_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def binding():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1912_09327_gb300 import binding as b
+    return b
+
+
+def run_gpu(binding, prob, nsteps):
+    d = binding.Domain.from_problem(prob)
+    d.step(nsteps)
+    out = d.moments()
+    res = d.residual() if nsteps > 0 else None
+    d.close()
+    return out, res
+
+
+def velocity_error(a, b):
+    ua = np.stack([a[1] / a[0], a[2] / a[0]])
+    ub = np.stack([b[1] / b[0], b[2] / b[0]])
+    return np.abs(ua - ub).max() / np.abs(ub).max()
+
+
+def test_channel_64x32_5000_steps(binding):
+    """Poiseuille channel, 64 x 32, 5000 steps, u_max ~ 0.01."""
+    p = wl.channel(64, 32, 0.01)
+    g, (res, mass) = run_gpu(binding, p, 5000)
+    o = oracle.run(p.mask, *p.state(), 5000, p.periodic, p.force)
+    err = velocity_error(g, o)
+    assert err <= 1e-5, err
+    fluid = p.mask == 0
+    # sum of FP32 rho - 1 over 5000 steps: within the FP32 unit roundoff
+    assert mass == pytest.approx(o[0][fluid].sum(), rel=1e-7)
+
+
+SIZES = [(1, 1), (2, 3), (3, 5), (4, 4), (17, 13), (121, 37), (119, 129),
+         (250, 131), (241, 300), (480, 129)]
+
+
+@pytest.mark.parametrize("nx,ny", SIZES)
+@pytest.mark.parametrize("periodic", [(True, True), (False, False),
+                                      (True, False), (False, True)])
+def test_random_domains(binding, nx, ny, periodic):
+    """Random node types (solid 20 %, fixed 5 %), random state, force, every
+    periodicity, sizes spanning several 120 x 128 tiles and ragged tails."""
+    amp, n = 0.02, 20
+    p = wl.random_problem(nx, ny, seed=nx * 1000 + ny, amp=amp,
+                          periodic=periodic, force=(1e-4, -5e-5))
+    g, _ = run_gpu(binding, p, n)
+    o = oracle.run(p.mask, *p.state(), n, p.periodic, p.force)
+    tol = 4e-7 * amp * n + 1e-9
+    for a, b in zip(g, o):
+        assert np.abs(a - b).max() <= tol
+
+
+def test_single_step_exact_paths(binding):
+    """One step on an all-fluid periodic box and on a walled box: every node
+    is compared with the oracle."""
+    for per in [(True, True), (False, False)]:
+        p = wl.random_problem(300, 200, seed=5, p_solid=0.0, p_fixed=0.0,
+                              amp=0.05, periodic=per, force=(0.0, 0.0))
+        g, _ = run_gpu(binding, p, 1)
+        o = oracle.step(p.mask, *p.state(), p.periodic, p.force)
+        for a, b in zip(g, o):
+            assert np.abs(a - b).max() <= 4e-7 * 0.05 + 1e-9
+
+
+def sample_nodes(shape, count, seed=0):
+    rng = np.random.default_rng(seed)
+    return rng.choice(shape[0] * shape[1], size=count, replace=False)
+
+
+def test_cavity_1024_full_size(binding):
+    """Lid-driven cavity 1024^2, lid u = 0.1: every node against the oracle
+    after 2000 steps; then the 20000-step run of the bench configuration,
+    checked for stability, a shrinking residual, and one more step on 20000
+    sampled nodes against the oracle's single-node update."""
+    oracle.set_threads(oracle.max_threads())
+    p = wl.cavity(1024, 0.1)
+    d = binding.Domain.from_problem(p)
+    d.step(2000)
+    g = d.moments()
+    o = oracle.run(p.mask, *p.state(), 2000, p.periodic, p.force)
+    assert velocity_error(g, o) <= 1e-5
+    assert np.abs(g[0] - o[0]).max() <= 1e-6
+    res_prev = None
+    for _ in range(9):
+        d.step(2000)
+        res, _ = d.residual()
+        assert np.isfinite(res)
+        if res_prev is not None:
+            assert res < res_prev
+        res_prev = res
+    d.step(1999)
+    before = d.moments()
+    d.step(1)
+    after = d.moments()
+    nodes = sample_nodes(p.mask.shape, 20000)
+    ref = oracle.step_nodes(p.mask, *before, nodes, p.periodic, p.force)
+    for f in range(3):
+        got = after[f].ravel()[nodes]
+        assert np.abs(got - ref[:, f]).max() <= 4e-7 * 0.1 + 1e-9
+    d.close()
+
+
+def test_porous_4096_full_size(binding):
+    """Periodic porous medium 4096^2 (seeded discs, solid fraction 0.30,
+    f_x = 1e-5): every node against the oracle after 20 steps, then a
+    single-step sampled check after 2000 steps, and the Reynolds number of the
+    flow stays below 1."""
+    oracle.set_threads(oracle.max_threads())
+    p = wl.porous(4096, seed=0)
+    d = binding.Domain.from_problem(p)
+    d.step(20)
+    g = d.moments()
+    o = oracle.run(p.mask, *p.state(), 20, p.periodic, p.force)
+    for a, b in zip(g, o):
+        assert np.abs(a - b).max() <= 4e-7 * 1e-3 * 20 + 1e-9
+    d.step(1979)
+    before = d.moments()
+    d.step(1)
+    after = d.moments()
+    nodes = sample_nodes(p.mask.shape, 20000, seed=1)
+    ref = oracle.step_nodes(p.mask, *before, nodes, p.periodic, p.force)
+    for f in range(3):
+        assert np.abs(after[f].ravel()[nodes] - ref[:, f]).max() <= 1e-9
+    fluid = p.mask == 0
+    u_mean = (after[1][fluid] / after[0][fluid]).mean()
+    Re = u_mean * p.meta["mean_diameter"] / wl.NU
+    assert 0 < Re < 1
+    d.close()
+
+
+def test_largest_sweep_domain_sampled(binding):
+    """16384^2 all-fluid periodic box (the largest bandwidth-sweep domain):
+    one step from a random state, 50000 sampled nodes against the oracle."""
+    n = 16384
+    rng = np.random.default_rng(7)
+    amp = 1e-3
+    st = [(amp * rng.standard_normal((n, n), dtype=np.float32))
+          for _ in range(3)]
+    mask = np.zeros((n, n), np.uint8)
+    d = binding.Domain(n, n, (True, True), (0.0, 0.0))
+    d.set_geometry(mask)
+    d.set_state(*st)
+    d.step(1)
+    nodes = sample_nodes((n, n), 50000, seed=2)
+    R0 = 1.0 + st[0].astype(np.float64)
+    ref = oracle.step_nodes(mask, R0, st[1].astype(np.float64),
+                            st[2].astype(np.float64), nodes, (True, True))
+    del R0
+    got = d.get_state()
+    d.close()
+    assert np.abs(got[0].ravel()[nodes] + 1.0 - ref[:, 0]).max() <= 1e-9
+    assert np.abs(got[1].ravel()[nodes] - ref[:, 1]).max() <= 1e-9
+    assert np.abs(got[2].ravel()[nodes] - ref[:, 2]).max() <= 1e-9
+
+
+def test_periodic_invariants_gpu(binding):
+    """All-fluid periodic box: mass conserved, total momentum grows by N*f
+    per step (to FP32 roundoff)."""
+    p = wl.periodic_box(257, 190, seed=4, amp=1e-2)
+    force = (2e-5, -1e-5)
+    d = binding.Domain(257, 190, (True, True), force)
+    d.set_geometry(p.mask)
+    d.set_moments(*p.state())
+    m0 = p.rho.sum()
+    jx0, jy0 = p.jx.sum(), p.jy.sum()
+    n = 100
+    d.step(n)
+    _, mass = d.residual()
+    R, U, V = d.moments()
+    N = p.mask.size
+    assert abs(mass - m0) / m0 < 1e-7
+    assert abs(R.sum() - m0) / m0 < 1e-7
+    assert abs(U.sum() - jx0 - n * N * force[0]) < 1e-7 * N * 1e-2
+    assert abs(V.sum() - jy0 - n * N * force[1]) < 1e-7 * N * 1e-2
+    d.close()
+
+
+def test_quiescent_is_bit_exact(binding):
+    """rho = 1, u = 0, no force: every field stays exactly zero in storage
+    (rho - 1 = 0, j = 0) whatever the geometry."""
+    for seed, per in [(1, (True, True)), (2, (False, False)), (3, (True, False))]:
+        mask = wl.random_mask((131, 245), seed, 0.3, 0.1)
+        d = binding.Domain(245, 131, per, (0.0, 0.0))
+        d.set_geometry(mask)
+        d.step(17)
+        for a in d.get_state():
+            assert not np.any(a)
+        d.close()
+
+
+def test_checkpoint_resume_is_bitwise(binding):
+    p = wl.random_problem(300, 170, seed=8, periodic=(True, False))
+    full = binding.Domain.from_problem(p)
+    full.step(60)
+    want = full.get_state()
+    a = binding.Domain.from_problem(p)
+    a.step(37)
+    saved = a.get_state()
+    b = binding.Domain(300, 170, p.periodic, p.force)
+    b.set_geometry(p.mask)
+    b.set_state(*saved)
+    b.step(23)
+    got = b.get_state()
+    for x, y in zip(got, want):
+        assert np.array_equal(x, y)
+    for dom in (full, a, b):
+        dom.close()
+
+
+def test_deterministic(binding):
+    p = wl.porous(512, seed=3)
+    outs = []
+    for _ in range(2):
+        d = binding.Domain.from_problem(p)
+        d.step(301)
+        outs.append((d.get_state(), d.residual()))
+        d.close()
+    for x, y in zip(outs[0][0], outs[1][0]):
+        assert np.array_equal(x, y)
+    assert outs[0][1] == outs[1][1]
+
+
+def test_unstable_state_is_reported(binding):
+    """Failure detection on the host side: a state with a non-finite or
+    negative density makes the reduced step raise the sticky flag, which
+    lbm_residual reports as LBM_E_UNSTABLE; loading a valid state clears it."""
+    p = wl.random_problem(64, 40, seed=2, periodic=(True, True))
+    for bad in (np.nan, -0.5):
+        d = binding.Domain.from_problem(p)
+        rho = p.rho.copy()
+        rho[20, 30] = bad
+        d.set_moments(rho, p.jx, p.jy)
+        d.step(3)
+        with pytest.raises(binding.LbmError) as e:
+            d.residual()
+        assert e.value.status == binding.LBM_E_UNSTABLE
+        d.set_moments(p.rho, p.jx, p.jy)
+        d.step(3)
+        res, mass = d.residual()
+        assert np.isfinite(res)
+        d.close()
+
+
+def test_residual_matches_oracle(binding):
+    p = wl.random_problem(200, 150, seed=6, amp=0.02, periodic=(False, True))
+    d = binding.Domain.from_problem(p)
+    d.step(40)
+    res, mass = d.residual()
+    d.close()
+    o_prev = oracle.run(p.mask, *p.state(), 39, p.periodic, p.force)
+    o_new = oracle.step(p.mask, *o_prev, p.periodic, p.force)
+    r_ref, m_ref = oracle.residual(p.mask, o_prev, o_new)
+    assert res == pytest.approx(r_ref, rel=1e-4)
+    assert mass == pytest.approx(m_ref, rel=1e-7)
+
+
+def test_independent_streams(binding):
+    """Two domains stepped on two streams, interleaved, give the same bits as
+    each run alone."""
+    import torch
+    p1 = wl.random_problem(333, 222, seed=11, periodic=(True, False))
+    p2 = wl.cavity(300, 0.05)
+    alone = []
+    for p in (p1, p2):
+        d = binding.Domain.from_problem(p)
+        d.step(50)
+        alone.append(d.get_state())
+        d.close()
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    d1 = binding.Domain.from_problem(p1, stream=s1)
+    d2 = binding.Domain.from_problem(p2, stream=s2)
+    for _ in range(10):
+        d1.step(5)
+        d2.step(5)
+    for d, want in ((d1, alone[0]), (d2, alone[1])):
+        for x, y in zip(d.get_state(), want):
+            assert np.array_equal(x, y)
+        d.close()
