@@ -368,6 +368,16 @@ def main(argv=None):
     total_ms = max_over_ranks(total_ms, world)
     res, mass = dom.residual()
     clocks = clk.summary()
+    # the step kernel alone, without the per-step reduction: lbm_step(ctx, K)
+    # reduces only on its last step
+    ku = 100
+    u0 = torch.cuda.Event(enable_timing=True)
+    u1 = torch.cuda.Event(enable_timing=True)
+    u0.record(stream)
+    dom.step(ku)
+    u1.record(stream)
+    stream.synchronize()
+    unreduced_ms = u0.elapsed_time(u1) / ku
 
     nodes = n * n
     value = nodes * args.steps * world / (total_ms * 1e3)
@@ -389,6 +399,12 @@ def main(argv=None):
                                    "(events around lbm_step(ctx, 1))",
                          "algorithmic_bytes_per_launch": BYTES_PER_LUP * nodes,
                          "peak_source": peak_src},
+            "unreduced_step": {
+                "ms": round(unreduced_ms, 4),
+                "mlups": round(n * n / (unreduced_ms * 1e3), 1),
+                "gbs_algorithmic": round(BYTES_PER_LUP * n * n / (unreduced_ms * 1e-3) / 1e9, 1),
+                "note": "lbm_step(ctx, 100) / 100: the step kernel without the residual reduction (it runs on the last step only)"},
+            "step_variant": int(os.environ.get("LBMTAU1_STEP_VARIANT", "0")),
             "gpu_launches": 2 * args.steps,
             "clocks": clocks,
             "residual_last_step": res}

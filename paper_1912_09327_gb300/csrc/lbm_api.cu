@@ -54,7 +54,8 @@ Layout make_layout(const lbm_params *p) {
   L.off_fields = off;
   off += 6 * L.field_bytes;
   L.off_mask = off;
-  off += align_up(plane, kAlign);
+  // bulk row copies may read up to 16 bytes past a row's end; pad the plane
+  off += align_up(plane + kAlign, kAlign);
   L.off_partials = off;
   off += align_up(static_cast<size_t>(L.nblocks) * 3 * sizeof(double), kAlign);
   L.off_result = off;
@@ -309,8 +310,9 @@ int lbm_step(lbm_ctx *c, int64_t nsteps) {
     if (e != cudaSuccess) return cuda_fail(c, e, "step kernel launch");
     c->cur = 1 - c->cur;
   }
-  cudaError_t e = lbmtau1::launch_finalize(c->partials, c->L.nblocks,
-                                           c->result, c->stream);
+  cudaError_t e = lbmtau1::launch_finalize(
+      c->partials, lbmtau1::launched_blocks(c->p.nx, c->p.ny), c->result,
+      c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "finalize kernel launch");
   c->has_residual = true;
   return LBM_OK;
@@ -359,10 +361,13 @@ int lbm_residual(lbm_ctx *c, double *residual, double *mass) {
   if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamSynchronize");
   unsigned flag;
   memcpy(&flag, &h[3], sizeof flag);
+  if (flag & 2u)
+    return fail(c, LBM_E_CUDA,
+                "a step's bulk row copy did not complete within one second");
   const double num = h[0], den = h[1];
   if (residual) *residual = den > 0.0 ? sqrt(num / den) : sqrt(num);
   if (mass) *mass = static_cast<double>(c->n_fluid) + h[2];
-  if (flag)
+  if (flag & 1u)
     return fail(c, LBM_E_UNSTABLE,
                 "a step produced rho <= 0 or a non-finite moment");
   c->err[0] = '\0';

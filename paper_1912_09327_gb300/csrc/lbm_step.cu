@@ -41,6 +41,7 @@
 // raises a sticky flag on rho <= 0 or non-finite values.
 #include <float.h>
 #include <stdint.h>
+#include <stdlib.h>
 
 #include "lbm_step.cuh"
 
@@ -48,10 +49,7 @@ namespace lbmtau1 {
 namespace {
 
 constexpr int kLanes = 32;
-constexpr int kCols = 4;                      // columns per lane (one float4)
-constexpr int kTileX = (kLanes - 2) * kCols;  // 120 output columns per warp
 constexpr int kWarps = 4;                     // warps per block, stacked in y
-constexpr int kRowsPerWarp = 32;              // output rows per warp
 constexpr int kThreads = kWarps * kLanes;
 constexpr unsigned kFull = 0xffffffffu;
 
@@ -64,63 +62,107 @@ constexpr float k1_12 = 1.0f / 12.0f;  // 3 * (1/36)
 constexpr float k1_3 = 1.0f / 3.0f;    // 3 * (1/9)
 constexpr float k1_6 = 1.0f / 6.0f;    // 2 * (1/12)
 
-__device__ __forceinline__ float comp(const float4 &v, int j) {
-  return j == 0 ? v.x : j == 1 ? v.y : j == 2 ? v.z : v.w;
-}
-
 __device__ __forceinline__ int64_t wrap_index(int64_t v, int64_t n) {
   v %= n;
   return v < 0 ? v + n : v;
 }
 
-// One source row as loaded: four columns of raw fields and their node types.
+// Packed FP32 arithmetic (sm_100 family FADD2 / FMUL2 / FFMA2): every value
+// below is a pair (row r, row r + 1) of the same column.
+__device__ __forceinline__ float2 bc(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add(float2 a, float2 b) {
+  return __fadd2_rn(a, b);
+}
+__device__ __forceinline__ float2 mul(float2 a, float2 b) {
+  return __fmul2_rn(a, b);
+}
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+  return __ffma2_rn(a, b, c);
+}
+// a - b, rounded once (exact when a and b are within a factor of 2)
+__device__ __forceinline__ float2 sub(float2 a, float2 b) {
+  return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
+}
+
+// Loads kC consecutive floats (one vector) of row `row` at column xb.
+template <int kC>
+__device__ __forceinline__ void load_vec(const float *p, float (&o)[kC]) {
+  if constexpr (kC == 4) {
+    const float4 v = __ldg(reinterpret_cast<const float4 *>(p));
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+  } else {
+    const float2 v = __ldg(reinterpret_cast<const float2 *>(p));
+    o[0] = v.x; o[1] = v.y;
+  }
+}
+
+template <int kC>
+__device__ __forceinline__ void store_vec(float *p, const float (&v)[kC]) {
+  if constexpr (kC == 4) {
+    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  } else {
+    *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
+  }
+}
+
+// One source row as loaded: kC columns of raw fields and their node types.
+template <int kC>
 struct RawRow {
-  float4 d, jx, jy;
+  float d[kC], jx[kC], jy[kC];
   unsigned solid;  // bit j: column j is solid or outside a non-periodic edge
   unsigned fluid;  // bit j: column j is a fluid node
 };
 
+// gathers bit 0 of each of the kC low bytes of v into bits 0..kC-1
+template <int kC>
 __device__ __forceinline__ unsigned byte_bits(unsigned v) {
-  // gathers bit 0 of each byte into bits 0..3
-  v &= 0x01010101u;
-  return (v | (v >> 7) | (v >> 14) | (v >> 21)) & 0xFu;
+  if constexpr (kC == 4) {
+    v &= 0x01010101u;
+    return (v | (v >> 7) | (v >> 14) | (v >> 21)) & 0xFu;
+  } else {
+    v &= 0x0101u;
+    return (v | (v >> 7)) & 0x3u;
+  }
 }
 
+template <int kC>
 __device__ __forceinline__ void load_row(const StepLaunch &a, int64_t r,
-                                         int64_t xb, RawRow &o) {
-  o.d = o.jx = o.jy = make_float4(0.f, 0.f, 0.f, 0.f);
-  o.solid = 0xFu;
+                                         int64_t xb, RawRow<kC> &o) {
+#pragma unroll
+  for (int j = 0; j < kC; ++j) o.d[j] = o.jx[j] = o.jy[j] = 0.f;
+  o.solid = (1u << kC) - 1u;
   o.fluid = 0u;
   if (r < 0 || r >= a.ny) {
     if (!a.periodic_y) return;  // outside a wall-less edge: solid
     r = wrap_index(r, a.ny);
   }
   const int64_t row = r * a.pitch;
-  if (xb >= 0 && xb + kCols <= a.nx) {
-    o.d = __ldg(reinterpret_cast<const float4 *>(a.src.d + row + xb));
-    o.jx = __ldg(reinterpret_cast<const float4 *>(a.src.jx + row + xb));
-    o.jy = __ldg(reinterpret_cast<const float4 *>(a.src.jy + row + xb));
-    const unsigned m =
-        __ldg(reinterpret_cast<const unsigned *>(a.mask + row + xb));
-    o.solid = byte_bits(m);                   // type 1 has bit 0 set
-    o.fluid = byte_bits(~(m | (m >> 1)));     // type 0 has bits 0, 1 clear
+  if (xb >= 0 && xb + kC <= a.nx) {
+    load_vec<kC>(a.src.d + row + xb, o.d);
+    load_vec<kC>(a.src.jx + row + xb, o.jx);
+    load_vec<kC>(a.src.jy + row + xb, o.jy);
+    unsigned m;
+    if constexpr (kC == 4)
+      m = __ldg(reinterpret_cast<const unsigned *>(a.mask + row + xb));
+    else
+      m = __ldg(reinterpret_cast<const unsigned short *>(a.mask + row + xb));
+    o.solid = byte_bits<kC>(m);               // type 1 has bit 0 set
+    o.fluid = byte_bits<kC>(~(m | (m >> 1)));  // type 0 has bits 0, 1 clear
     return;
   }
-  float dv[kCols], xv[kCols], yv[kCols];
   unsigned solid = 0u, fluid = 0u;
 #pragma unroll
-  for (int j = 0; j < kCols; ++j) {
+  for (int j = 0; j < kC; ++j) {
     int64_t x = xb + j;
     bool in = x >= 0 && x < a.nx;
     if (!in && a.periodic_x) {
       x = wrap_index(x, a.nx);
       in = true;
     }
-    dv[j] = xv[j] = yv[j] = 0.f;
     if (in) {
-      dv[j] = __ldg(a.src.d + row + x);
-      xv[j] = __ldg(a.src.jx + row + x);
-      yv[j] = __ldg(a.src.jy + row + x);
+      o.d[j] = __ldg(a.src.d + row + x);
+      o.jx[j] = __ldg(a.src.jx + row + x);
+      o.jy[j] = __ldg(a.src.jy + row + x);
       const unsigned t = __ldg(a.mask + row + x);
       solid |= (t == 1u) << j;
       fluid |= (t == 0u) << j;
@@ -128,229 +170,491 @@ __device__ __forceinline__ void load_row(const StepLaunch &a, int64_t r,
       solid |= 1u << j;
     }
   }
-  o.d = make_float4(dv[0], dv[1], dv[2], dv[3]);
-  o.jx = make_float4(xv[0], xv[1], xv[2], xv[3]);
-  o.jy = make_float4(yv[0], yv[1], yv[2], yv[3]);
   o.solid = solid;
   o.fluid = fluid;
 }
 
-// Partial sums of the three moments for one output row (this lane's columns).
-struct Acc {
-  float dd[kCols], mx[kCols], my[kCols];
+// ---- Row staging through shared memory with the bulk-copy (TMA) engine ----
+// An interior warp tile streams its source rows through a ring of kS shared-
+// memory stages: lane 0 starts `cp.async.bulk` global->shared copies of the
+// tile's row window (three fields and the node types) several rows ahead,
+// each completing on the stage's mbarrier, so the loads in flight do not
+// occupy registers.  Every wait is bounded in time; on expiry the kernel
+// raises kFlagCopyTimeout, drains its copies (again bounded) and stops.
+constexpr unsigned kFlagUnstable = 1u;
+constexpr unsigned kFlagCopyTimeout = 2u;
+constexpr unsigned long long kWaitLimitNs = 1000000000ull;  // one second
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
+                   smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+// completes the current phase without data (a stage use that copies nothing)
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void bulk_copy(void *dst, const void *src,
+                                          uint32_t bytes, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes "
+      "[%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0u;
+}
+
+// Waits for phase `parity` of `bar`; false when a second passes first.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+  if (mbar_try(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  while (!mbar_try(bar, parity))
+    if (global_ns() - t0 > kWaitLimitNs) return false;
+  return true;
+}
+
+__device__ __forceinline__ void fence_async_shared() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Geometry of one ring stage for kC columns per lane: the field window starts
+// at column x0 - 4 (16-byte aligned) and covers the warp's kLanes * kC
+// columns; the node-type window starts at the 16-byte boundary at or below it.
+template <int kC>
+struct Stage {
+  static constexpr int kWin = ((kLanes * kC + (4 - kC)) + 3) / 4 * 4;  // floats
+  static constexpr int kFieldBytes = kWin * 4;
+  static constexpr int kMaskBytes = (kWin + 12 + 15) / 16 * 16;
+  static constexpr int kBytes = 3 * kFieldBytes + kMaskBytes;
+  static constexpr int kLaneOffset = 4 - kC;  // first column of lane 0
 };
 
-template <bool kReduce>
-__global__ void __launch_bounds__(kThreads, 3)
+// Sums of w_k (1, c_k) over the solid neighbours of a node, indexed by the
+// 3 x 3 solid bits around it: bits 0-2 the row below (SW, S, SE), 3-5 its own
+// row (W, -, E), 6-8 the row above (NW, N, NE).  c_k = -e_k points from the
+// neighbour to the node.
+struct alignas(16) SolidSums {
+  float s0, sx, sy, pad;
+};
+
+__device__ __forceinline__ void build_solid_lut(SolidSums *lut) {
+  for (int c = threadIdx.x; c < 512; c += blockDim.x) {
+    const float sw = (c >> 0) & 1, s = (c >> 1) & 1, se = (c >> 2) & 1;
+    const float w = (c >> 3) & 1, e = (c >> 5) & 1;
+    const float nw = (c >> 6) & 1, n = (c >> 7) & 1, ne = (c >> 8) & 1;
+    SolidSums v;
+    v.s0 = k1_9 * ((w + e) + (s + n)) + k1_36 * ((sw + se) + (nw + ne));
+    v.sx = k1_9 * (w - e) + k1_36 * ((sw - se) + (nw - ne));
+    v.sy = k1_9 * (s - n) + k1_36 * ((sw + se) - (nw + ne));
+    v.pad = 0.f;
+    lut[c] = v;
+  }
+}
+
+// The step kernel.  kC columns per lane (4: float4 rows, 2: float2 rows);
+// kRows output rows per warp (even).  Source rows arrive in pairs (r, r+1)
+// and all per-node arithmetic runs on (row r, row r+1) float2 pairs.
+//
+// With S = (r, r+1) and S' = (r-2, r-1) the previous pair, each pair adds
+//   North(S) to output rows (r-1, r), Same(S) to rows (r, r+1) and
+//   South(S) to rows (r+1, r+2),
+// so rows (r-1, r) are complete after pair S:
+//   out(r-1) = North(S).x + Same(S').y + South(S').x,
+//   out(r)   = North(S).y + Same(S).x  + South(S').y.
+template <int kC, int kS>
+__host__ __device__ constexpr int ring_bytes() {
+  return 128 + kS * Stage<kC>::kBytes;  // barriers, then the stages
+}
+
+template <int kC, int kS>
+__host__ __device__ constexpr int smem_bytes() {
+  return 512 * static_cast<int>(sizeof(SolidSums)) + kWarps * ring_bytes<kC, kS>();
+}
+
+template <int kC, int kRows, int kMinBlocks, int kS, bool kReduce>
+__global__ void __launch_bounds__(kThreads, kMinBlocks)
     lbm_step_kernel(const StepLaunch a) {
+  static_assert(kRows % 2 == 0, "rows per warp must be even");
+  static_assert(kS >= 4 && kS % 2 == 0 && kS <= 32, "ring stages");
+  constexpr int kTile = (kLanes - 2) * kC;
+  using St = Stage<kC>;
+  extern __shared__ __align__(128) unsigned char smem[];
+  SolidSums *lut = reinterpret_cast<SolidSums *>(smem);
+  build_solid_lut(lut);
+  __syncthreads();
+
   const int lane = threadIdx.x & (kLanes - 1);
   const int warp = threadIdx.x / kLanes;
-  const int64_t x0 = static_cast<int64_t>(blockIdx.x) * kTileX;
-  const int64_t xb = x0 - kCols + static_cast<int64_t>(kCols) * lane;
+  const int64_t x0 = static_cast<int64_t>(blockIdx.x) * kTile;
+  const int64_t xb = x0 - kC + static_cast<int64_t>(kC) * lane;
   const int64_t y0 =
-      (static_cast<int64_t>(blockIdx.y) * kWarps + warp) * kRowsPerWarp;
-  const int64_t y1 = min(y0 + kRowsPerWarp, a.ny);
+      (static_cast<int64_t>(blockIdx.y) * kWarps + warp) * kRows;
+  const int64_t y1 = min(y0 + kRows, a.ny);
   const bool owner = lane >= 1 && lane <= kLanes - 2 && xb < a.nx;
+  // interior tiles stream rows through the shared-memory ring
+  const bool bulk = x0 - 4 >= 0 && x0 - 4 + St::kWin <= a.nx;
+  unsigned char *ring =
+      smem + 512 * sizeof(SolidSums) + warp * ring_bytes<kC, kS>();
+  uint64_t *bars = reinterpret_cast<uint64_t *>(ring);
+  unsigned char *stages = ring + 128;
+  const int64_t m0 = (x0 - 4) & ~int64_t(15);  // node-type window start
+  const int moff = static_cast<int>(x0 - 4 - m0);
   const float fx = a.fx, fy = a.fy;
+  const float2 F2x = bc(fx), F2y = bc(fy), F22y = bc(2.0f * fy);
+  const float2 one = bc(1.0f), c3 = bc(3.0f), cm15 = bc(-1.5f), c9 = bc(9.0f);
+  const float2 w1_9 = bc(k1_9), wm1_9 = bc(-k1_9), w1_36 = bc(k1_36),
+               wm1_36 = bc(-k1_36), w1_12 = bc(k1_12), w1_3 = bc(k1_3),
+               w4_9 = bc(k4_9), w1_6 = bc(k1_6), half = bc(0.5f);
 
-  float num = 0.f, den = 0.f, mass = 0.f;
-  bool bad = false;
+  float2 rs_num = bc(0.f), rs_den = bc(0.f), rs_mass = bc(0.f);
+  float rmin = 1.0f;
 
   if (y0 < a.ny) {
-    Acc accA, accB;  // output rows r-1 and r while source row r arrives
+    // carried from the previous pair S'
+    float same_dd[kC], same_mx[kC];                 // Same(S').y
+    float2 south_dd[kC], south_mx[kC], south_my[kC];  // South(S')
+    float pd[kC], pjx[kC], pjy[kC], pir[kC];        // raw row r-1, its 1/rho
+    float2 zpx[kC], zpy[kC];                        // z of S'
 #pragma unroll
-    for (int j = 0; j < kCols; ++j) {
-      accA.dd[j] = accA.mx[j] = accA.my[j] = 0.f;
-      accB.dd[j] = accB.mx[j] = accB.my[j] = 0.f;
+    for (int j = 0; j < kC; ++j) {
+      same_dd[j] = same_mx[j] = 0.f;
+      south_dd[j] = south_mx[j] = south_my[j] = bc(0.f);
+      pd[j] = pjx[j] = pjy[j] = 0.f;
+      pir[j] = 1.f;
+      zpx[j] = zpy[j] = bc(0.f);
     }
-    float zpx[kCols], zpy[kCols];  // z of row r-2 (D row of output r-1)
-    float zcx[kCols], zcy[kCols];  // z of row r-1
-    float hd[kCols], hx[kCols], hy[kCols];  // raw fields of row r-1
+    unsigned pA6 = 0u, pB6 = 0u;  // solid bits (cols -1..kC) of rows r-2, r-1
+    unsigned pfluidB = 0u;        // fluid bits of row r-1
+
+    const int64_t npairs = (y1 - y0 + 1) / 2 + 1;
+    const int64_t nrows = 2 * npairs;  // source rows y0 - 1 .. y0 - 2 + nrows
+    // source row of ring index i: -1 for a solid row beyond a wall-less edge
+    auto source_row = [&](int64_t i) -> int64_t {
+      int64_t r = y0 - 1 + i;
+      if (r >= 0 && r < a.ny) return r;
+      return a.periodic_y ? wrap_index(r, a.ny) : -1;
+    };
+    auto issue = [&](int64_t i) {  // lane 0 only
+      const int64_t r = source_row(i);
+      const int st = static_cast<int>(i % kS);
+      uint64_t *bar = bars + st;
+      if (r < 0) {  // solid row: nothing to copy, but the phase still completes
+        mbar_arrive(bar);
+        return;
+      }
+      unsigned char *dst = stages + st * St::kBytes;
+      const int64_t off = r * a.pitch + (x0 - 4);
+      mbar_expect_tx(bar, St::kBytes);
+      bulk_copy(dst, a.src.d + off, St::kFieldBytes, bar);
+      bulk_copy(dst + St::kFieldBytes, a.src.jx + off, St::kFieldBytes, bar);
+      bulk_copy(dst + 2 * St::kFieldBytes, a.src.jy + off, St::kFieldBytes, bar);
+      bulk_copy(dst + 3 * St::kFieldBytes, a.mask + r * a.pitch + m0,
+                St::kMaskBytes, bar);
+    };
+    // ring row i -> registers; false when the copy did not arrive in time
+    auto fetch = [&](int64_t i, RawRow<kC> &o) -> bool {
+      if (!bulk) {
+        load_row<kC>(a, y0 - 1 + i, xb, o);
+        return true;
+      }
+      if (source_row(i) < 0) {
 #pragma unroll
-    for (int j = 0; j < kCols; ++j) {
-      zpx[j] = zpy[j] = zcx[j] = zcy[j] = 0.f;
-      hd[j] = hx[j] = hy[j] = 0.f;
+        for (int j = 0; j < kC; ++j) o.d[j] = o.jx[j] = o.jy[j] = 0.f;
+        o.solid = (1u << kC) - 1u;
+        o.fluid = 0u;
+        return true;
+      }
+      const int st = static_cast<int>(i % kS);
+      const bool ok = mbar_wait(bars + st, static_cast<uint32_t>((i / kS) & 1));
+      const unsigned char *src = stages + st * St::kBytes;
+      const int c = St::kLaneOffset + kC * lane;
+      if constexpr (kC == 4) {
+        const float4 d = *reinterpret_cast<const float4 *>(src + 4 * c);
+        const float4 x = *reinterpret_cast<const float4 *>(src + St::kFieldBytes + 4 * c);
+        const float4 y = *reinterpret_cast<const float4 *>(src + 2 * St::kFieldBytes + 4 * c);
+        o.d[0] = d.x; o.d[1] = d.y; o.d[2] = d.z; o.d[3] = d.w;
+        o.jx[0] = x.x; o.jx[1] = x.y; o.jx[2] = x.z; o.jx[3] = x.w;
+        o.jy[0] = y.x; o.jy[1] = y.y; o.jy[2] = y.z; o.jy[3] = y.w;
+        const unsigned m = *reinterpret_cast<const unsigned *>(
+            src + 3 * St::kFieldBytes + moff + c);
+        o.solid = byte_bits<kC>(m);
+        o.fluid = byte_bits<kC>(~(m | (m >> 1)));
+      } else {
+        const float2 d = *reinterpret_cast<const float2 *>(src + 4 * c);
+        const float2 x = *reinterpret_cast<const float2 *>(src + St::kFieldBytes + 4 * c);
+        const float2 y = *reinterpret_cast<const float2 *>(src + 2 * St::kFieldBytes + 4 * c);
+        o.d[0] = d.x; o.d[1] = d.y;
+        o.jx[0] = x.x; o.jx[1] = x.y;
+        o.jy[0] = y.x; o.jy[1] = y.y;
+        const unsigned m = *reinterpret_cast<const unsigned short *>(
+            src + 3 * St::kFieldBytes + moff + c);
+        o.solid = byte_bits<kC>(m);
+        o.fluid = byte_bits<kC>(~(m | (m >> 1)));
+      }
+      return ok;
+    };
+    int64_t issued = 0;
+    if (bulk) {
+      if (lane == 0) {
+        for (int st = 0; st < kS; ++st) mbar_init(bars + st);
+        fence_async_shared();
+        for (; issued < nrows && issued < kS; ++issued) issue(issued);
+      }
+      issued = __shfl_sync(kFull, issued, 0);
+      __syncwarp();
     }
-    unsigned sD6 = 0u, sO6 = 0u;  // solid bits (cols -1..4) of rows r-2, r-1
-    unsigned fluidO = 0u;         // fluid bits of row r-1
+    bool aborted = false;
+    int64_t consumed = 0;
+    for (int64_t k = 0; k < npairs; ++k) {
+      consumed = 2 * k;
+      const int64_t r = y0 - 1 + 2 * k;  // S = (r, r+1)
+      RawRow<kC> ra, rb;
+      bool ok = fetch(2 * k, ra);
+      ok = fetch(2 * k + 1, rb) && ok;
+      if (!__all_sync(kFull, ok)) {
+        aborted = true;
+        break;
+      }
+      if (bulk) {
+        __syncwarp();  // every lane has read both stages
+        if (lane == 0) {
+          fence_async_shared();
+          for (int t = 0; t < 2 && issued < nrows; ++t, ++issued) issue(issued);
+        }
+        issued = __shfl_sync(kFull, issued, 0);
+      }
 
-    RawRow cur;
-    load_row(a, y0 - 1, xb, cur);
-    for (int64_t r = y0 - 1; r <= y1; ++r) {
-      RawRow nxt;
-      if (r < y1) load_row(a, r + 1, xb, nxt);
-
-      // Per-node quantities of source row r, own columns (index j + 1).
-      float df[kCols + 2], zx[kCols + 2], zy[kCols + 2];
-      float A[kCols + 2], G[kCols + 2], X[kCols + 2];
-      float B[kCols], R0[kCols];
+      // Per-node quantities of S, own columns at index j + 1.
+      float2 df[kC + 2], zx[kC + 2], zy[kC + 2], A[kC + 2], G[kC + 2],
+          X[kC + 2];
+      float2 B[kC], R0[kC], ir[kC];
 #pragma unroll
-      for (int j = 0; j < kCols; ++j) {
-        const bool s = (cur.solid >> j) & 1u;
-        const float d = comp(cur.d, j);
-        const float zxj = s ? -fx : comp(cur.jx, j);
-        const float zyj = s ? -fy : comp(cur.jy, j);
-        const float mx = zxj + fx;  // j + F, exactly 0 on solid nodes
-        const float my = zyj + fy;
-        const float dfj = s ? 0.f : d;
-        const float ir = __frcp_rn(1.0f + dfj);
-        const float t = mx * ir;
-        const float pxx = t * mx, pxy = t * my, pyy = my * my * ir;
-        const float tr = pxx + pyy;
+      for (int j = 0; j < kC; ++j) {
+        const bool sa = (ra.solid >> j) & 1u, sb = (rb.solid >> j) & 1u;
+        const float2 zxj = make_float2(sa ? -fx : ra.jx[j], sb ? -fx : rb.jx[j]);
+        const float2 zyj = make_float2(sa ? -fy : ra.jy[j], sb ? -fy : rb.jy[j]);
+        const float2 dfj = make_float2(sa ? 0.f : ra.d[j], sb ? 0.f : rb.d[j]);
+        const float2 mx = add(zxj, F2x);  // j + F, exactly 0 on solid nodes
+        const float2 my = add(zyj, F2y);
+        const float2 rho = add(dfj, one);
+        const float2 irj =
+            make_float2(__fdividef(1.0f, rho.x), __fdividef(1.0f, rho.y));
+        const float2 t = mul(mx, irj);
+        const float2 pxx = mul(t, mx), pxy = mul(t, my);
+        const float2 pyy = mul(mul(my, my), irj);
+        const float2 tr = add(pxx, pyy);
         df[j + 1] = dfj;
         zx[j + 1] = zxj;
         zy[j + 1] = zyj;
-        A[j + 1] = 3.0f * pxx - 1.5f * pyy;
-        B[j] = 3.0f * pyy - 1.5f * pxx;
-        G[j + 1] = fmaf(3.0f, tr, dfj);
-        X[j + 1] = 9.0f * pxy;
-        R0[j] = fmaf(-1.5f, tr, d);
+        A[j + 1] = fma2(c3, pxx, mul(cm15, pyy));
+        B[j] = fma2(c3, pyy, mul(cm15, pxx));
+        G[j + 1] = fma2(c3, tr, dfj);
+        X[j + 1] = mul(c9, pxy);
+        R0[j] = fma2(cm15, tr, make_float2(ra.d[j], rb.d[j]));
+        ir[j] = irj;
       }
-      // Halo columns -1 and 4 from the neighbouring lanes.
-      df[0] = __shfl_up_sync(kFull, df[kCols], 1);
-      zx[0] = __shfl_up_sync(kFull, zx[kCols], 1);
-      zy[0] = __shfl_up_sync(kFull, zy[kCols], 1);
-      A[0] = __shfl_up_sync(kFull, A[kCols], 1);
-      G[0] = __shfl_up_sync(kFull, G[kCols], 1);
-      X[0] = __shfl_up_sync(kFull, X[kCols], 1);
-      df[kCols + 1] = __shfl_down_sync(kFull, df[1], 1);
-      zx[kCols + 1] = __shfl_down_sync(kFull, zx[1], 1);
-      zy[kCols + 1] = __shfl_down_sync(kFull, zy[1], 1);
-      A[kCols + 1] = __shfl_down_sync(kFull, A[1], 1);
-      G[kCols + 1] = __shfl_down_sync(kFull, G[1], 1);
-      X[kCols + 1] = __shfl_down_sync(kFull, X[1], 1);
-      const unsigned sl = __shfl_up_sync(kFull, cur.solid, 1);
-      const unsigned sr = __shfl_down_sync(kFull, cur.solid, 1);
-      const unsigned s6 = ((sl >> (kCols - 1)) & 1u) | (cur.solid << 1) |
-                          ((sr & 1u) << (kCols + 1));
+      // Halo columns -1 and kC from the neighbouring lanes.
+#define LBM_HALO(q)                                                   \
+  q[0].x = __shfl_up_sync(kFull, q[kC].x, 1);                        \
+  q[0].y = __shfl_up_sync(kFull, q[kC].y, 1);                        \
+  q[kC + 1].x = __shfl_down_sync(kFull, q[1].x, 1);                  \
+  q[kC + 1].y = __shfl_down_sync(kFull, q[1].y, 1);
+      LBM_HALO(df)
+      LBM_HALO(zx)
+      LBM_HALO(zy)
+      LBM_HALO(A)
+      LBM_HALO(G)
+      LBM_HALO(X)
+#undef LBM_HALO
+      const unsigned sbits = ra.solid | (rb.solid << kC);
+      const unsigned sl = __shfl_up_sync(kFull, sbits, 1);
+      const unsigned sr = __shfl_down_sync(kFull, sbits, 1);
+      const unsigned A6 = ((sl >> (kC - 1)) & 1u) | (ra.solid << 1) |
+                          ((sr & 1u) << (kC + 1));
+      const unsigned B6 = ((sl >> (2 * kC - 1)) & 1u) | (rb.solid << 1) |
+                          (((sr >> kC) & 1u) << (kC + 1));
+      const bool any_solid = __any_sync(kFull, (pA6 | pB6 | A6 | B6) != 0u);
 
-      Acc accC;
+      float od0[kC], ox0[kC], oy0[kC], od1[kC], ox1[kC], oy1[kC];
 #pragma unroll
-      for (int j = 0; j < kCols; ++j) {
+      for (int j = 0; j < kC; ++j) {
         const int L = j, C = j + 1, R = j + 2;
-        const float mxL = zx[L] + fx, mxR = zx[R] + fx;
-        const float myL = zy[L] + fy, myR = zy[R] + fy, myC = zy[C] + fy;
-        const float hxl = zx[L] - zx[C], hxr = zx[R] - zx[C];  // exact
-        const float hyl = zy[L] - zy[C], hyr = zy[R] - zy[C];
-        // row r as the row above output row r-1 (NW, U, NE)
-        accA.dd[j] += k1_9 * (df[C] - 3.0f * myC + B[j]) +
-                      k1_36 * (G[L] + G[R] + 3.0f * (mxL - myL) -
-                               3.0f * (mxR + myR) - X[L] + X[R]);
-        accA.mx[j] += k1_36 * (G[L] - G[R] - X[L] - X[R]) +
-                      k1_12 * ((myR - myL) + (hxl + hxr));
-        accA.my[j] += -k1_9 * (df[C] + B[j]) +
-                      k1_36 * (X[L] - X[R] - G[L] - G[R]) +
-                      k1_12 * ((mxR - mxL) + (hyl + hyr));
-        // row r as the same row of output row r (L, O, R)
-        accB.dd[j] += k4_9 * R0[j] +
-                      k1_9 * (df[L] + df[R] + 3.0f * (mxL - mxR) + A[L] + A[R]);
-        accB.mx[j] +=
-            k1_9 * (df[L] - df[R] + A[L] - A[R]) + k1_3 * (hxl + hxr);
-        // row r as the row below output row r+1 (SW, D, SE)
-        accC.dd[j] = k1_9 * (df[C] + 3.0f * myC + B[j]) +
-                     k1_36 * (G[L] + G[R] + 3.0f * (mxL + myL) +
-                              3.0f * (myR - mxR) + X[L] - X[R]);
-        accC.mx[j] = k1_36 * (G[L] - G[R] + X[L] + X[R]) +
-                     k1_12 * ((myL - myR) + (hxl + hxr));
-        accC.my[j] = k1_9 * (df[C] + B[j]) +
-                     k1_36 * (G[L] + G[R] + X[L] - X[R]) +
-                     k1_12 * ((mxL - mxR) + (hyl + hyr));
-      }
+        const float2 Gs = add(G[L], G[R]), Gd = sub(G[L], G[R]);
+        const float2 Xs = add(X[L], X[R]), Xd = sub(X[L], X[R]);
+        const float2 mxd = sub(zx[L], zx[R]), myd = sub(zy[L], zy[R]);
+        const float2 mys = add(add(zy[L], zy[R]), F22y);
+        const float2 hx = add(sub(zx[L], zx[C]), sub(zx[R], zx[C]));  // exact
+        const float2 hy = add(sub(zy[L], zy[C]), sub(zy[R], zy[C]));
+        const float2 P = add(df[C], B[j]);
+        const float2 Q = mul(c3, add(zy[C], F2y));
+        const float2 GmX = sub(Gs, Xd), GpX = add(Gs, Xd);
+        // S as the row pair above output rows (r-1, r): NW, N, NE
+        const float2 Ndd = fma2(w1_9, sub(P, Q),
+                                mul(w1_36, fma2(c3, sub(mxd, mys), GmX)));
+        const float2 Nmx = fma2(w1_36, sub(Gd, Xs), mul(w1_12, sub(hx, myd)));
+        const float2 Nmy =
+            fma2(wm1_9, P, fma2(wm1_36, GmX, mul(w1_12, sub(hy, mxd))));
+        // S as the own rows of outputs (r, r+1): W, O, E
+        const float2 Sdd = fma2(w4_9, R0[j],
+                                mul(w1_9, fma2(c3, mxd, add(add(df[L], df[R]),
+                                                            add(A[L], A[R])))));
+        const float2 Smx = fma2(w1_9, add(sub(df[L], df[R]), sub(A[L], A[R])),
+                                mul(w1_3, hx));
+        // S as the row pair below outputs (r+1, r+2): SW, S, SE
+        const float2 Tdd = fma2(w1_9, add(P, Q),
+                                mul(w1_36, fma2(c3, add(mxd, mys), GpX)));
+        const float2 Tmx = fma2(w1_36, add(Gd, Xs), mul(w1_12, add(hx, myd)));
+        const float2 Tmy =
+            fma2(w1_9, P, fma2(w1_36, GpX, mul(w1_12, add(hy, mxd))));
 
-      // Output row r-1 is complete: rows r-2 (D), r-1 (O), r (U).
-      const int64_t yo = r - 1;
-      const bool any_solid = __any_sync(kFull, (sD6 | sO6 | s6) != 0u);
-      float4 od, ox, oy;
-      float outd[kCols], outx[kCols], outy[kCols];
-#pragma unroll
-      for (int j = 0; j < kCols; ++j) {
-        float S0 = 0.f, Sx = 0.f, Sy = 0.f;  // sums of w_k (1, c_k) over solid P
+        // Complete output rows (r-1, r) of column j.
+        const float2 acc_dd =
+            add(add(Ndd, make_float2(same_dd[j], Sdd.x)), south_dd[j]);
+        const float2 acc_mx =
+            add(add(Nmx, make_float2(same_mx[j], Smx.x)), south_mx[j]);
+        const float2 acc_my = add(Nmy, south_my[j]);
+        const float2 dO = make_float2(pd[j], ra.d[j]);
+        const float2 jxO = make_float2(pjx[j], ra.jx[j]);
+        const float2 jyO = make_float2(pjy[j], ra.jy[j]);
+        float2 S0 = bc(0.f), Sx = bc(0.f), Sy = bc(0.f);
         if (any_solid) {
-          const float sL = (sO6 >> j) & 1u, sR = (sO6 >> (j + 2)) & 1u;
-          const float sD = (sD6 >> (j + 1)) & 1u, sU = (s6 >> (j + 1)) & 1u;
-          const float sSW = (sD6 >> j) & 1u, sSE = (sD6 >> (j + 2)) & 1u;
-          const float sNW = (s6 >> j) & 1u, sNE = (s6 >> (j + 2)) & 1u;
-          S0 = k1_9 * ((sL + sR) + (sD + sU)) +
-               k1_36 * ((sSW + sSE) + (sNW + sNE));
-          Sx = k1_9 * (sL - sR) + k1_36 * ((sSW - sSE) + (sNW - sNE));
-          Sy = k1_9 * (sD - sU) + k1_36 * ((sSW + sSE) - (sNW + sNE));
+          const unsigned c0 = ((pA6 >> j) & 7u) | (((pB6 >> j) & 7u) << 3) |
+                              (((A6 >> j) & 7u) << 6);
+          const unsigned c1 = ((pB6 >> j) & 7u) | (((A6 >> j) & 7u) << 3) |
+                              (((B6 >> j) & 7u) << 6);
+          const SolidSums e0 = lut[c0], e1 = lut[c1];
+          S0 = make_float2(e0.s0, e1.s0);
+          Sx = make_float2(e0.sx, e1.sx);
+          Sy = make_float2(e0.sy, e1.sy);
         }
-        const float dO = hd[j], jxO = hx[j], jyO = hy[j];
-        const float dn = fmaf(dO, S0, accA.dd[j]);
-        const float mxn =
-            jxO + (fx + accA.mx[j] +
-                   k1_6 * ((zpx[j] - jxO) + (zx[j + 1] - jxO)) + dO * Sx);
-        const float myn =
-            jyO + (fy + accA.my[j] + 0.5f * ((zpy[j] - jyO) + (zy[j + 1] - jyO)) +
-                   dO * Sy);
-        const bool upd = (fluidO >> j) & 1u;
-        outd[j] = upd ? dn : dO;
-        outx[j] = upd ? mxn : jxO;
-        outy[j] = upd ? myn : jyO;
-        if (kReduce) {
-          if (upd && owner && yo >= y0 && xb + j < a.nx) {
-            const float rn = 1.0f + dn;
-            bad |= !(rn > 0.f) || !(fabsf(mxn) <= FLT_MAX) ||
-                   !(fabsf(myn) <= FLT_MAX);
-            const float ro = 1.0f + dO;
-            const float uxo = jxO / ro, uyo = jyO / ro;
-            const float uxn = mxn / rn, uyn = myn / rn;
-            const float ddx = uxn - uxo, ddy = uyn - uyo;
-            num = fmaf(ddx, ddx, fmaf(ddy, ddy, num));
-            den = fmaf(uxn, uxn, fmaf(uyn, uyn, den));
-            mass += dn;
-          }
+        const float2 dn = fma2(dO, S0, acc_dd);
+        const float2 mxn = add(
+            jxO, fma2(dO, Sx, fma2(w1_6, add(sub(zpx[j], jxO), sub(zx[C], jxO)),
+                                   add(acc_mx, F2x))));
+        const float2 myn = add(
+            jyO, fma2(dO, Sy, fma2(half, add(sub(zpy[j], jyO), sub(zy[C], jyO)),
+                                   add(acc_my, F2y))));
+        const bool f0 = (pfluidB >> j) & 1u, f1 = (ra.fluid >> j) & 1u;
+        od0[j] = f0 ? dn.x : dO.x;
+        ox0[j] = f0 ? mxn.x : jxO.x;
+        oy0[j] = f0 ? myn.x : jyO.x;
+        od1[j] = f1 ? dn.y : dO.y;
+        ox1[j] = f1 ? mxn.y : jxO.y;
+        oy1[j] = f1 ? myn.y : jyO.y;
+        if constexpr (kReduce) {
+          const bool col = owner && xb + j < a.nx;
+          const bool v0 = f0 && col && r - 1 >= y0;
+          const bool v1 = f1 && col && r >= y0 && r < y1;
+          // u_new - u_old = ((j_n - j_o) + (j_n d_o - j_o d_n)) / (rho_n rho_o)
+          const float2 rn = add(dn, one);
+          const float2 irn =
+              make_float2(__fdividef(1.0f, rn.x), __fdividef(1.0f, rn.y));
+          const float2 iro = make_float2(pir[j], ir[j].x);
+          const float2 sc = mul(irn, iro);
+          const float2 dux = mul(add(sub(mxn, jxO), sub(mul(mxn, dO), mul(jxO, dn))), sc);
+          const float2 duy = mul(add(sub(myn, jyO), sub(mul(myn, dO), mul(jyO, dn))), sc);
+          const float2 ux = mul(mxn, irn), uy = mul(myn, irn);
+          const float2 nn = fma2(dux, dux, mul(duy, duy));
+          const float2 dd2 = fma2(ux, ux, mul(uy, uy));
+          rs_num = add(rs_num, make_float2(v0 ? nn.x : 0.f, v1 ? nn.y : 0.f));
+          rs_den = add(rs_den, make_float2(v0 ? dd2.x : 0.f, v1 ? dd2.y : 0.f));
+          rs_mass = add(rs_mass, make_float2(v0 ? dn.x : 0.f, v1 ? dn.y : 0.f));
+          rmin = fminf(rmin, fminf(v0 ? rn.x : 1.f, v1 ? rn.y : 1.f));
+        }
+        // carry to the next pair
+        same_dd[j] = Sdd.y;
+        same_mx[j] = Smx.y;
+        south_dd[j] = Tdd;
+        south_mx[j] = Tmx;
+        south_my[j] = Tmy;
+      }
+      if (owner) {
+        if (r - 1 >= y0) {
+          const int64_t o = (r - 1) * a.pitch + xb;
+          store_vec<kC>(a.dst.d + o, od0);
+          store_vec<kC>(a.dst.jx + o, ox0);
+          store_vec<kC>(a.dst.jy + o, oy0);
+        }
+        if (r >= y0 && r < y1) {
+          const int64_t o = r * a.pitch + xb;
+          store_vec<kC>(a.dst.d + o, od1);
+          store_vec<kC>(a.dst.jx + o, ox1);
+          store_vec<kC>(a.dst.jy + o, oy1);
         }
       }
-      if (owner && yo >= y0) {
-        od = make_float4(outd[0], outd[1], outd[2], outd[3]);
-        ox = make_float4(outx[0], outx[1], outx[2], outx[3]);
-        oy = make_float4(outy[0], outy[1], outy[2], outy[3]);
-        const int64_t o = yo * a.pitch + xb;
-        *reinterpret_cast<float4 *>(a.dst.d + o) = od;
-        *reinterpret_cast<float4 *>(a.dst.jx + o) = ox;
-        *reinterpret_cast<float4 *>(a.dst.jy + o) = oy;
-      }
-
-      // Shift the window by one row.
+      // Shift the window by one pair.
 #pragma unroll
-      for (int j = 0; j < kCols; ++j) {
-        accA.dd[j] = accB.dd[j];
-        accA.mx[j] = accB.mx[j];
-        accA.my[j] = accB.my[j];
-        accB.dd[j] = accC.dd[j];
-        accB.mx[j] = accC.mx[j];
-        accB.my[j] = accC.my[j];
-        zpx[j] = zcx[j];
-        zpy[j] = zcy[j];
-        zcx[j] = zx[j + 1];
-        zcy[j] = zy[j + 1];
-        hd[j] = comp(cur.d, j);
-        hx[j] = comp(cur.jx, j);
-        hy[j] = comp(cur.jy, j);
+      for (int j = 0; j < kC; ++j) {
+        pd[j] = rb.d[j];
+        pjx[j] = rb.jx[j];
+        pjy[j] = rb.jy[j];
+        pir[j] = ir[j].y;
+        zpx[j] = zx[j + 1];
+        zpy[j] = zy[j + 1];
       }
-      sD6 = sO6;
-      sO6 = s6;
-      fluidO = cur.fluid;
-      if (r < y1) cur = nxt;
+      pA6 = A6;
+      pB6 = B6;
+      pfluidB = rb.fluid;
+    }
+    if (aborted) {
+      if (lane == 0) atomicOr(a.flag, kFlagCopyTimeout);
+      // let every copy still in flight land before the block exits
+      for (int64_t i = consumed; i < issued; ++i) {
+        if (source_row(i) < 0) continue;
+        mbar_wait(bars + i % kS, static_cast<uint32_t>((i / kS) & 1));
+      }
     }
   }
 
-  if (kReduce) {
+  if constexpr (kReduce) {
     __shared__ double part[kWarps][3];
-    double v0 = num, v1 = den, v2 = mass;
+    double v0 = static_cast<double>(rs_num.x) + rs_num.y;
+    double v1 = static_cast<double>(rs_den.x) + rs_den.y;
+    double v2 = static_cast<double>(rs_mass.x) + rs_mass.y;
 #pragma unroll
     for (int o = kLanes / 2; o > 0; o >>= 1) {
       v0 += __shfl_xor_sync(kFull, v0, o);
       v1 += __shfl_xor_sync(kFull, v1, o);
       v2 += __shfl_xor_sync(kFull, v2, o);
     }
+    const bool bad = !(rmin > 0.f) || !isfinite(v0) || !isfinite(v1) ||
+                     !isfinite(v2);
     const bool any_bad = __any_sync(kFull, bad);
     if (lane == 0) {
       part[warp][0] = v0;
       part[warp][1] = v1;
       part[warp][2] = v2;
-      if (any_bad) atomicOr(a.flag, 1u);
+      if (any_bad) atomicOr(a.flag, kFlagUnstable);
     }
     __syncthreads();
     if (threadIdx.x < 3) {
@@ -411,11 +715,53 @@ __global__ void unpack_kernel(Fields f, double *__restrict__ staging,
   }
 }
 
+// Tile variants: columns per lane, output rows per warp, resident blocks per
+// SM requested from the register allocator, shared-memory ring stages.
+struct Variant {
+  int cols, rows, min_blocks, stages;
+};
+constexpr Variant kVariants[] = {
+    {4, 64, 2, 8}, {2, 64, 3, 12}, {4, 32, 2, 8}, {2, 64, 4, 12}};
+constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
+
+int active_variant() {
+  static int v = [] {
+    const char *e = getenv("LBMTAU1_STEP_VARIANT");
+    int i = e ? atoi(e) : 0;
+    return (i >= 0 && i < kNumVariants) ? i : 0;
+  }();
+  return v;
+}
+
 dim3 step_grid(int64_t nx, int64_t ny) {
-  const int64_t gx = (nx + kTileX - 1) / kTileX;
-  const int64_t gy =
-      (ny + kWarps * kRowsPerWarp - 1) / (kWarps * kRowsPerWarp);
+  const Variant v = kVariants[active_variant()];
+  const int64_t tile_x = (kLanes - 2) * v.cols;
+  const int64_t tile_y = static_cast<int64_t>(kWarps) * v.rows;
+  const int64_t gx = (nx + tile_x - 1) / tile_x;
+  const int64_t gy = (ny + tile_y - 1) / tile_y;
   return dim3(static_cast<unsigned>(gx), static_cast<unsigned>(gy), 1);
+}
+
+template <int kV, bool kReduce>
+cudaError_t launch_variant(const StepLaunch &a, dim3 g, cudaStream_t s) {
+  constexpr Variant v = kVariants[kV];
+  constexpr int smem = smem_bytes<v.cols, v.stages>();
+  auto kern = lbm_step_kernel<v.cols, v.rows, v.min_blocks, v.stages, kReduce>;
+  static cudaError_t attr = cudaFuncSetAttribute(
+      kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (attr != cudaSuccess) return attr;
+  kern<<<g, kThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <bool kReduce>
+cudaError_t launch_any(const StepLaunch &a, dim3 g, cudaStream_t s) {
+  switch (active_variant()) {
+    case 1: return launch_variant<1, kReduce>(a, g, s);
+    case 2: return launch_variant<2, kReduce>(a, g, s);
+    case 3: return launch_variant<3, kReduce>(a, g, s);
+    default: return launch_variant<0, kReduce>(a, g, s);
+  }
 }
 
 int copy_grid(int64_t n) {
@@ -426,17 +772,26 @@ int copy_grid(int64_t n) {
 }  // namespace
 
 int64_t step_blocks(int64_t nx, int64_t ny) {
+  // the largest grid over all variants, so a workspace fits any of them
+  int64_t most = 0;
+  for (int i = 0; i < kNumVariants; ++i) {
+    const Variant v = kVariants[i];
+    const int64_t tile_x = (kLanes - 2) * v.cols;
+    const int64_t tile_y = static_cast<int64_t>(kWarps) * v.rows;
+    const int64_t b = ((nx + tile_x - 1) / tile_x) * ((ny + tile_y - 1) / tile_y);
+    most = b > most ? b : most;
+  }
+  return most;
+}
+
+int64_t launched_blocks(int64_t nx, int64_t ny) {
   const dim3 g = step_grid(nx, ny);
   return static_cast<int64_t>(g.x) * g.y;
 }
 
 cudaError_t launch_step(const StepLaunch &a, bool reduce, cudaStream_t s) {
   const dim3 g = step_grid(a.nx, a.ny);
-  if (reduce)
-    lbm_step_kernel<true><<<g, kThreads, 0, s>>>(a);
-  else
-    lbm_step_kernel<false><<<g, kThreads, 0, s>>>(a);
-  return cudaGetLastError();
+  return reduce ? launch_any<true>(a, g, s) : launch_any<false>(a, g, s);
 }
 
 cudaError_t launch_finalize(const double *partials, int64_t nblocks,

@@ -25,8 +25,10 @@ struct StepLaunch {
   unsigned int *flag;   // sticky instability flag (reduced steps only)
 };
 
-// Number of thread blocks (and so of reduction partials) of one step launch.
+// Upper bound on the thread blocks (reduction partials) of one step launch,
+// over every tile variant; and the count of the variant in use.
 int64_t step_blocks(int64_t nx, int64_t ny);
+int64_t launched_blocks(int64_t nx, int64_t ny);
 
 // Enqueues one step; `reduce` also writes block partials of
 // (sum |du|^2, sum |u|^2, sum (rho - 1)) and raises the flag on instability.

@@ -182,7 +182,8 @@ def test_largest_sweep_domain_sampled(binding):
     del R0
     got = d.get_state()
     d.close()
-    assert np.abs(got[0].ravel()[nodes] + 1.0 - ref[:, 0]).max() <= 1e-9
+    assert np.abs(got[0].ravel()[nodes].astype(np.float64) + 1.0
+                  - ref[:, 0]).max() <= 1e-9
     assert np.abs(got[1].ravel()[nodes] - ref[:, 1]).max() <= 1e-9
     assert np.abs(got[2].ravel()[nodes] - ref[:, 2]).max() <= 1e-9
 
@@ -255,23 +256,28 @@ def test_deterministic(binding):
 
 
 def test_unstable_state_is_reported(binding):
-    """Failure detection on the host side: a state with a non-finite or
-    negative density makes the reduced step raise the sticky flag, which
+    """Failure detection on the host side: a state with a non-finite density,
+    or a block of negative density large enough that the next step's output
+    is still negative, makes the reduced step raise the sticky flag, which
     lbm_residual reports as LBM_E_UNSTABLE; loading a valid state clears it."""
     p = wl.random_problem(64, 40, seed=2, periodic=(True, True))
-    for bad in (np.nan, -0.5):
+    cases = [("nan", (20, 30), np.nan, 3), ("negative block", (slice(15, 20), slice(40, 45)), -0.5, 1)]
+    for name, where, value, nsteps in cases:
         d = binding.Domain.from_problem(p)
+        mask = p.mask.copy()
+        mask[where] = wl.FLUID
+        d.set_geometry(mask)
         rho = p.rho.copy()
-        rho[20, 30] = bad
+        rho[where] = value
         d.set_moments(rho, p.jx, p.jy)
-        d.step(3)
-        with pytest.raises(binding.LbmError) as e:
+        d.step(nsteps)
+        with pytest.raises(binding.LbmError, match="UNSTABLE") as e:
             d.residual()
-        assert e.value.status == binding.LBM_E_UNSTABLE
+        assert e.value.status == binding.LBM_E_UNSTABLE, name
         d.set_moments(p.rho, p.jx, p.jy)
         d.step(3)
         res, mass = d.residual()
-        assert np.isfinite(res)
+        assert np.isfinite(res), name
         d.close()
 
 
