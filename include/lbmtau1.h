@@ -157,6 +157,45 @@ int lbm_set_state(lbm_ctx *ctx, const void *drho, const void *jx,
  */
 int lbm_residual(lbm_ctx *ctx, double *residual, double *mass);
 
+/*
+ * One step that allocates no memory (the paper has no counterpart; this is
+ * an interface for callers that cannot allocate device memory themselves,
+ * such as an application that hands all device memory to its own pool
+ * allocator and forbids side allocations, or a loop with a hard latency
+ * budget where cudaMalloc / cudaFree are not acceptable).
+ *
+ * Runs one reduced LBMTau1 step, the same kernel as lbm_step, from
+ * caller-owned device fields (rho - 1, jx, jy as float32, rows of `pitch`
+ * elements) into a second caller-owned set, with the node types in a
+ * caller-owned uint8 array of the same pitch.  It calls no cudaMalloc,
+ * cudaFree or allocating library routine: the reduction scratch is a
+ * file-scope device array of 1.5 MB (2^16 blocks x 3 doubles) that every GPU
+ * loading this library holds until the process exits.
+ *   Inputs:  drho_in, jx_in, jy_in, mask (all 16-byte aligned; pitch >= nx,
+ *            pitch % 32 == 0; the mask buffer needs 256 bytes of slack after
+ *            its last row, which bulk copies of aligned windows may read).
+ *   Outputs: drho_out, jx_out, jy_out (same layout; columns nx..pitch-1 may be
+ *            overwritten), dev_sums = device array of 3 doubles receiving
+ *            sum |u_n - u_{n-1}|^2, sum |u_n|^2 and sum (rho_n - 1) over fluid
+ *            nodes, dev_flags = device uint32 receiving 0 or a nonzero flag
+ *            (bit 0: rho <= 0 or a non-finite moment; bit 1: a bulk row copy
+ *            did not complete within one second).
+ * Asynchronous on cuda_stream.  The first call on each device resolves the
+ * scratch array's device address (cudaGetSymbolAddress) and configures the
+ * kernel; make that first call before any stream capture.  All calls share
+ * the one scratch array, so calls that overlap on the GPU (for instance on
+ * two streams) race; the array keeps the last call's contents, and the call
+ * clears what must start at zero.
+ * Errors: LBM_E_INVAL (null or misaligned pointer, bad size, or a domain
+ * needing more than 2^16 thread blocks), LBM_E_CUDA.
+ */
+int lbm_step_noalloc(const float *drho_in, const float *jx_in,
+                     const float *jy_in, float *drho_out, float *jx_out,
+                     float *jy_out, const uint8_t *mask, int64_t nx,
+                     int64_t ny, int64_t pitch, int32_t periodic_x,
+                     int32_t periodic_y, double fx, double fy,
+                     double *dev_sums, uint32_t *dev_flags, void *cuda_stream);
+
 /* Frees the context's host state; the workspace stays the caller's. */
 void lbm_destroy(lbm_ctx *ctx);
 

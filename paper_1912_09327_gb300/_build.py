@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "liblbmtau1.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["lbm_step.cu", "lbm_api.cu"]
+SOURCES = ["lbm_step.cu", "lbm_api.cu", "lbm_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -61,6 +61,9 @@ _lib.lbm_set_state.restype = ctypes.c_int
 _lib.lbm_residual.argtypes = [_vp, ctypes.POINTER(ctypes.c_double),
                               ctypes.POINTER(ctypes.c_double)]
 _lib.lbm_residual.restype = ctypes.c_int
+_lib.lbm_step_noalloc.argtypes = [_vp] * 7 + [ctypes.c_int64] * 3 + \
+    [ctypes.c_int32] * 2 + [ctypes.c_double] * 2 + [_vp, _vp, _vp]
+_lib.lbm_step_noalloc.restype = ctypes.c_int
 _lib.lbm_destroy.argtypes = [_vp]
 _lib.lbm_destroy.restype = None
 _lib.lbm_last_error.argtypes = [_vp]
@@ -164,6 +167,21 @@ def lbm_residual(ctx):
     st = _lib.lbm_residual(ctx, ctypes.byref(r), ctypes.byref(m))
     _check(st, ctx)
     return r.value, m.value
+
+
+def lbm_step_noalloc(drho_in, jx_in, jy_in, drho_out, jx_out, jy_out, mask,
+                     nx, ny, pitch, periodic, force, dev_sums, dev_flags,
+                     cuda_stream=0) -> None:
+    """One reduced step between caller-owned device buffers (addresses as
+    ints), with no allocation; see include/lbmtau1.h."""
+    st = _lib.lbm_step_noalloc(
+        *[_vp(int(p)) for p in (drho_in, jx_in, jy_in, drho_out, jx_out,
+                                 jy_out, mask)],
+        int(nx), int(ny), int(pitch), int(bool(periodic[0])),
+        int(bool(periodic[1])), float(force[0]), float(force[1]),
+        _vp(int(dev_sums)), _vp(int(dev_flags)), _vp(int(cuda_stream)))
+    if st != LBM_OK:
+        raise LbmError(st, "lbm_step_noalloc")
 
 
 def lbm_destroy(ctx) -> None:
