@@ -24,7 +24,9 @@
  *     equilibrium is formed (Algorithm 1): u = (U + fx) / rho.
  *   - Moments cross the ABI as density rho and momentum (jx, jy) = rho*u,
  *     the quantities Eqs. (rhotau1) and (utau1) evolve, in double precision.
- *     Device storage is FP32: rho - 1, jx, jy.
+ *     Device storage is FP32: rho - 1, jx, jy.  A solid node holds no fluid
+ *     state (the wall rule never reads it): the library stores rho - 1 = 0 and
+ *     j = -F there, and lbm_moments reports it at rest, rho = 1, j = 0.
  *   - Every call returns LBM_OK (0) or a negative status; nothing aborts or
  *     throws across the ABI.  lbm_last_error() describes the last failure.
  *   - All device work is enqueued on the CUDA stream given to lbm_create.
@@ -123,8 +125,8 @@ int lbm_step(lbm_ctx *ctx, int64_t nsteps);
 
 /*
  * Copies the current state to caller-owned host arrays of nx*ny doubles:
- * density, and momentum jx, jy (velocity = j / rho).  Solid and fixed nodes
- * return the values they hold.  Synchronises the stream.
+ * density, and momentum jx, jy (velocity = j / rho).  Fixed nodes return the
+ * values they hold, solid nodes rho = 1, j = 0.  Synchronises the stream.
  * Errors: LBM_E_INVAL, LBM_E_STATE, LBM_E_CUDA.
  */
 int lbm_moments(lbm_ctx *ctx, double *rho, double *jx, double *jy);
@@ -132,9 +134,10 @@ int lbm_moments(lbm_ctx *ctx, double *rho, double *jx, double *jy);
 /*
  * Exact state transfer in the device storage format, for checkpoint/resume:
  * three caller-owned host arrays of nx*ny elements (float for
- * LBM_STORAGE_F32) holding rho - 1, jx and jy exactly as stored.  A state
- * saved with lbm_get_state and loaded with lbm_set_state into a context with
- * the same parameters and geometry continues bit for bit.  lbm_get_state
+ * LBM_STORAGE_F32) holding rho - 1, jx and jy exactly as stored (solid
+ * nodes: 0, -fx, -fy; lbm_set_state writes those there whatever it is
+ * given).  A state saved with lbm_get_state and loaded with lbm_set_state
+ * into a context with the same parameters and geometry continues bit for bit.  lbm_get_state
  * synchronises; lbm_set_state returns once the host arrays have been read.
  * Errors: LBM_E_INVAL, LBM_E_STATE (no geometry yet), LBM_E_CUDA.
  */
@@ -172,6 +175,7 @@ int lbm_residual(lbm_ctx *ctx, double *residual, double *mass);
  * file-scope device array of 1.5 MB (2^16 blocks x 3 doubles) that every GPU
  * loading this library holds until the process exits.
  *   Inputs:  drho_in, jx_in, jy_in, mask (all 16-byte aligned; pitch >= nx,
+ *            the values held at solid nodes are never read;
  *            pitch % 32 == 0; the mask buffer needs 256 bytes of slack after
  *            its last row, which bulk copies of aligned windows may read).
  *   Outputs: drho_out, jx_out, jy_out (same layout; columns nx..pitch-1 may be

@@ -120,6 +120,15 @@ int bind_device(lbm_ctx *c) {
   return LBM_OK;
 }
 
+int apply_solid_storage(lbm_ctx *c, int copy) {
+  const int64_t n = c->L.pitch * c->p.ny;
+  cudaError_t e = lbmtau1::launch_solid_storage(
+      c->f[copy], c->mask, n, static_cast<float>(c->p.fx),
+      static_cast<float>(c->p.fy), c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "solid storage kernel");
+  return LBM_OK;
+}
+
 int reset_flags(lbm_ctx *c) {
   cudaError_t e = cudaMemsetAsync(c->result, 0, kAlign, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemsetAsync(result)");
@@ -194,6 +203,10 @@ int lbm_set_geometry(lbm_ctx *c, const uint8_t *host_mask) {
   e = cudaMemsetAsync(c->base + c->L.off_fields, 0, 6 * c->L.field_bytes,
                       c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemsetAsync(fields)");
+  for (int k = 0; k < 2; ++k) {
+    st = apply_solid_storage(c, k);
+    if (st) return st;
+  }
   st = reset_flags(c);
   if (st) return st;
   // the host mask may be released as soon as this call returns
@@ -230,6 +243,8 @@ int lbm_set_moments(lbm_ctx *c, const double *rho, const double *jx,
                                          c->L.pitch, y0, rows, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "pack kernel");
   }
+  st = apply_solid_storage(c, c->cur);
+  if (st) return st;
   st = reset_flags(c);
   if (st) return st;
   cudaError_t e = cudaStreamSynchronize(c->stream);
@@ -255,6 +270,8 @@ int lbm_set_state(lbm_ctx *c, const void *drho, const void *jx,
                                       cudaMemcpyHostToDevice, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpy2DAsync(H2D)");
   }
+  st = apply_solid_storage(c, c->cur);
+  if (st) return st;
   st = reset_flags(c);
   if (st) return st;
   cudaError_t e = cudaStreamSynchronize(c->stream);
@@ -330,8 +347,8 @@ int lbm_moments(lbm_ctx *c, double *rho, double *jx, double *jy) {
     const int64_t rows =
         y0 + c->L.staging_rows <= c->p.ny ? c->L.staging_rows : c->p.ny - y0;
     const size_t n = static_cast<size_t>(rows) * nx;
-    cudaError_t e = lbmtau1::launch_unpack(c->f[c->cur], c->staging, nx,
-                                           c->L.pitch, y0, rows, c->stream);
+    cudaError_t e = lbmtau1::launch_unpack(c->f[c->cur], c->mask, c->staging,
+                                           nx, c->L.pitch, y0, rows, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "unpack kernel");
     double *dst[3] = {rho, jx, jy};
     for (int k = 0; k < 3; ++k) {

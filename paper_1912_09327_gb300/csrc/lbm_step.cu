@@ -701,17 +701,31 @@ __global__ void pack_kernel(const double *__restrict__ staging, Fields f,
   }
 }
 
-__global__ void unpack_kernel(Fields f, double *__restrict__ staging,
-                              int64_t nx, int64_t pitch, int64_t y0,
-                              int64_t rows) {
+__global__ void unpack_kernel(Fields f, const uint8_t *__restrict__ mask,
+                              double *__restrict__ staging, int64_t nx,
+                              int64_t pitch, int64_t y0, int64_t rows) {
   const int64_t n = nx * rows;
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
        i < n; i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const int64_t y = y0 + i / nx, x = i % nx;
     const int64_t o = y * pitch + x;
-    staging[i] = 1.0 + static_cast<double>(f.d[o]);
-    staging[n + i] = static_cast<double>(f.jx[o]);
-    staging[2 * n + i] = static_cast<double>(f.jy[o]);
+    const bool solid = mask[o] == 1u;  // holds no fluid state: report rest
+    staging[i] = solid ? 1.0 : 1.0 + static_cast<double>(f.d[o]);
+    staging[n + i] = solid ? 0.0 : static_cast<double>(f.jx[o]);
+    staging[2 * n + i] = solid ? 0.0 : static_cast<double>(f.jy[o]);
+  }
+}
+
+// Writes the solid-node storage values rho - 1 = 0, j = -F.
+__global__ void solid_storage_kernel(Fields f, const uint8_t *__restrict__ mask,
+                                     int64_t n, float fx, float fy) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+       i < n; i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    if (mask[i] == 1u) {
+      f.d[i] = 0.f;
+      f.jx[i] = -fx;
+      f.jy[i] = -fy;
+    }
   }
 }
 
@@ -808,10 +822,17 @@ cudaError_t launch_pack(const double *staging, Fields f, int64_t nx,
   return cudaGetLastError();
 }
 
-cudaError_t launch_unpack(Fields f, double *staging, int64_t nx, int64_t pitch,
-                          int64_t y0, int64_t rows, cudaStream_t s) {
-  unpack_kernel<<<copy_grid(nx * rows), 256, 0, s>>>(f, staging, nx, pitch, y0,
-                                                     rows);
+cudaError_t launch_unpack(Fields f, const uint8_t *mask, double *staging,
+                          int64_t nx, int64_t pitch, int64_t y0, int64_t rows,
+                          cudaStream_t s) {
+  unpack_kernel<<<copy_grid(nx * rows), 256, 0, s>>>(f, mask, staging, nx,
+                                                     pitch, y0, rows);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_solid_storage(Fields f, const uint8_t *mask, int64_t n,
+                                 float fx, float fy, cudaStream_t s) {
+  solid_storage_kernel<<<copy_grid(n), 256, 0, s>>>(f, mask, n, fx, fy);
   return cudaGetLastError();
 }
 

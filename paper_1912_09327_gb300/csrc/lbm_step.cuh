@@ -43,7 +43,14 @@ cudaError_t launch_finalize(const double *partials, int64_t nblocks,
 cudaError_t launch_pack(const double *staging, Fields f, int64_t nx,
                         int64_t pitch, int64_t y0, int64_t rows,
                         cudaStream_t s);
-cudaError_t launch_unpack(Fields f, double *staging, int64_t nx, int64_t pitch,
-                          int64_t y0, int64_t rows, cudaStream_t s);
+cudaError_t launch_unpack(Fields f, const uint8_t *mask, double *staging,
+                          int64_t nx, int64_t pitch, int64_t y0, int64_t rows,
+                          cudaStream_t s);
+
+// Storage convention of the step kernel: a solid node holds rho - 1 = 0 and
+// j = -F (what a solid source contributes, with no test of the node type).
+// Writes those values into every solid node of f (n = pitch * ny entries).
+cudaError_t launch_solid_storage(Fields f, const uint8_t *mask, int64_t n,
+                                 float fx, float fy, cudaStream_t s);
 
 }  // namespace lbmtau1

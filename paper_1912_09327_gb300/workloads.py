@@ -143,7 +143,10 @@ def random_mask(shape, seed: int = 0, p_solid: float = 0.2,
 def random_problem(nx: int, ny: int, seed: int = 0, p_solid: float = 0.2,
                    p_fixed: float = 0.05, amp: float = 0.02,
                    periodic=(True, True), force=(1e-4, -5e-5)) -> Problem:
-    """Random node types and a random state: the general parity case."""
+    """Random node types and a random state on the non-solid nodes (solid
+    nodes hold no fluid state: rest, rho = 1): the general parity case."""
     mask = random_mask((ny, nx), seed, p_solid, p_fixed)
     r, u, v = random_state((ny, nx), seed + 1, amp)
+    solid = mask == SOLID
+    r[solid], u[solid], v[solid] = 1.0, 0.0, 0.0
     return Problem("random", mask, tuple(periodic), tuple(force), r, u, v)

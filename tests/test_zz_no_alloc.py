@@ -49,6 +49,8 @@ def test_noalloc_step_matches_lbm_step():
     bufs = [[torch.zeros((ny, pitch), **f32) for _ in range(3)] for _ in range(2)]
     init = [(p.rho - 1.0).astype(np.float32), p.jx.astype(np.float32),
             p.jy.astype(np.float32)]
+    solid = p.mask == wl.SOLID  # solid storage convention: 0, -fx, -fy
+    init[0][solid], init[1][solid], init[2][solid] = 0.0, -p.force[0], -p.force[1]
     for t, a in zip(bufs[0], init):
         t[:, :nx] = torch.from_numpy(a).to(dev)
     mask = torch.ones(ny * pitch + 256, dtype=torch.uint8, device=dev)
