@@ -203,6 +203,67 @@ int lbm_step_noalloc(const float *drho_in, const float *jx_in,
 /* Frees the context's host state; the workspace stays the caller's. */
 void lbm_destroy(lbm_ctx *ctx);
 
+/*
+ * Batches: one launch per time step for many independent domains.
+ *
+ * The paper steps one domain at a time; independent domains (Algorithm 1
+ * applied to each) can share a launch.  A batch references existing contexts
+ * (each with its own workspace, geometry and state) that use the batch's
+ * stream.  lbm_batch_step advances every member by nsteps with one launch per
+ * step over a work list of all members' block tiles, taken by a persistent
+ * grid through an atomic counter; runs of steps inside a call are replayed
+ * from a captured CUDA graph.  Each member ends bit for bit where it would
+ * have ended alone, and afterwards lbm_moments / lbm_residual / lbm_step work
+ * on it as usual (the last step of the call is reduced for every member).
+ */
+typedef struct lbm_batch lbm_batch;
+
+/* Device workspace of a batch of up to `capacity` members whose block tiles
+ * number at most `max_tiles` in total; 0 when the arguments are invalid. */
+size_t lbm_batch_workspace_bytes(int32_t capacity, int64_t max_tiles);
+
+/* Creates a batch over a caller-owned device workspace (256-byte aligned) on
+ * cuda_stream.  Errors: LBM_E_INVAL, LBM_E_WORKSPACE. */
+int lbm_batch_create(int32_t capacity, int64_t max_tiles, void *dev_workspace,
+                     size_t workspace_bytes, void *cuda_stream,
+                     lbm_batch **out);
+
+/* Adds a context (same stream as the batch, geometry set) and returns its
+ * slot; the context must outlive its membership.  Errors: LBM_E_INVAL,
+ * LBM_E_STATE, LBM_E_WORKSPACE (batch full). */
+int lbm_batch_add(lbm_batch *b, lbm_ctx *ctx, int32_t *slot);
+
+/* Removes the member in `slot` (between steps).  Errors: LBM_E_INVAL. */
+int lbm_batch_remove(lbm_batch *b, int32_t slot);
+
+/* Number of members. */
+int32_t lbm_batch_members(const lbm_batch *b);
+
+/* Advances every member by nsteps (asynchronous on the batch stream).
+ * Errors: LBM_E_INVAL, LBM_E_WORKSPACE (more tiles than the workspace holds),
+ * LBM_E_CUDA. */
+int lbm_batch_step(lbm_batch *b, int64_t nsteps);
+
+/* Tile variants (block tile shapes) of the step kernel: their count, and the
+ * one a batch uses.  All variants give bit-identical states. */
+int32_t lbm_variant_count(void);
+int lbm_batch_set_variant(lbm_batch *b, int32_t variant);
+int32_t lbm_batch_variant(const lbm_batch *b);
+
+/* Autotuner: times steps_per_variant (even, >= 2) batch steps, plus two
+ * warm-up steps, with every tile variant and keeps the fastest.  These are
+ * real steps: every member advances by (steps_per_variant + 2) times the
+ * variant count.  ms_per_step (NULL or lbm_variant_count() doubles) receives
+ * the measured time per step of each variant.  Synchronises the stream. */
+int lbm_batch_autotune(lbm_batch *b, int32_t steps_per_variant,
+                       int32_t *chosen, double *ms_per_step);
+
+/* Frees the batch's host state (members and workspace stay the caller's). */
+void lbm_batch_destroy(lbm_batch *b);
+
+/* Message for the last failed call on the batch. */
+const char *lbm_batch_last_error(const lbm_batch *b);
+
 /* Message for the last failed call on ctx ("" when none; static text for a
  * NULL ctx).  Valid until the next call on ctx. */
 const char *lbm_last_error(const lbm_ctx *ctx);

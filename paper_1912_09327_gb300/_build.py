@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "liblbmtau1.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["lbm_step.cu", "lbm_api.cu", "lbm_noalloc.cu"]
+SOURCES = ["lbm_step.cu", "lbm_api.cu", "lbm_noalloc.cu", "lbm_batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -39,7 +39,8 @@ def _cuda_lib() -> str:
 
 def _inputs():
     files = [os.path.join(CSRC, s) for s in SOURCES]
-    files += [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")]
+    files += [os.path.join(CSRC, f) for f in os.listdir(CSRC)
+              if f.endswith((".cuh", ".h"))]
     files.append(os.path.join(INCLUDE, "lbmtau1.h"))
     files.append(os.path.abspath(__file__))
     return files

@@ -64,6 +64,32 @@ _lib.lbm_residual.restype = ctypes.c_int
 _lib.lbm_step_noalloc.argtypes = [_vp] * 7 + [ctypes.c_int64] * 3 + \
     [ctypes.c_int32] * 2 + [ctypes.c_double] * 2 + [_vp, _vp, _vp]
 _lib.lbm_step_noalloc.restype = ctypes.c_int
+_lib.lbm_batch_workspace_bytes.argtypes = [ctypes.c_int32, ctypes.c_int64]
+_lib.lbm_batch_workspace_bytes.restype = ctypes.c_size_t
+_lib.lbm_batch_create.argtypes = [ctypes.c_int32, ctypes.c_int64, _vp,
+                                  ctypes.c_size_t, _vp, ctypes.POINTER(_vp)]
+_lib.lbm_batch_create.restype = ctypes.c_int
+_lib.lbm_batch_add.argtypes = [_vp, _vp, ctypes.POINTER(ctypes.c_int32)]
+_lib.lbm_batch_add.restype = ctypes.c_int
+_lib.lbm_batch_remove.argtypes = [_vp, ctypes.c_int32]
+_lib.lbm_batch_remove.restype = ctypes.c_int
+_lib.lbm_batch_members.argtypes = [_vp]
+_lib.lbm_batch_members.restype = ctypes.c_int32
+_lib.lbm_batch_step.argtypes = [_vp, ctypes.c_int64]
+_lib.lbm_batch_step.restype = ctypes.c_int
+_lib.lbm_variant_count.argtypes = []
+_lib.lbm_variant_count.restype = ctypes.c_int32
+_lib.lbm_batch_set_variant.argtypes = [_vp, ctypes.c_int32]
+_lib.lbm_batch_set_variant.restype = ctypes.c_int
+_lib.lbm_batch_variant.argtypes = [_vp]
+_lib.lbm_batch_variant.restype = ctypes.c_int32
+_lib.lbm_batch_autotune.argtypes = [_vp, ctypes.c_int32,
+                                    ctypes.POINTER(ctypes.c_int32), _vp]
+_lib.lbm_batch_autotune.restype = ctypes.c_int
+_lib.lbm_batch_destroy.argtypes = [_vp]
+_lib.lbm_batch_destroy.restype = None
+_lib.lbm_batch_last_error.argtypes = [_vp]
+_lib.lbm_batch_last_error.restype = ctypes.c_char_p
 _lib.lbm_destroy.argtypes = [_vp]
 _lib.lbm_destroy.restype = None
 _lib.lbm_last_error.argtypes = [_vp]
@@ -186,6 +212,118 @@ def lbm_step_noalloc(drho_in, jx_in, jy_in, drho_out, jx_out, jy_out, mask,
 
 def lbm_destroy(ctx) -> None:
     _lib.lbm_destroy(ctx)
+
+
+def _bcheck(status, b):
+    if status != LBM_OK:
+        raise LbmError(status, _lib.lbm_batch_last_error(b).decode())
+
+
+def lbm_batch_workspace_bytes(capacity: int, max_tiles: int) -> int:
+    return int(_lib.lbm_batch_workspace_bytes(int(capacity), int(max_tiles)))
+
+
+def lbm_batch_create(capacity, max_tiles, dev_workspace, workspace_bytes,
+                     cuda_stream=0):
+    b = _vp()
+    _check(_lib.lbm_batch_create(int(capacity), int(max_tiles),
+                                 _vp(dev_workspace), workspace_bytes,
+                                 _vp(cuda_stream), ctypes.byref(b)))
+    return b
+
+
+def lbm_batch_add(b, ctx) -> int:
+    slot = ctypes.c_int32()
+    _bcheck(_lib.lbm_batch_add(b, ctx, ctypes.byref(slot)), b)
+    return slot.value
+
+
+def lbm_batch_remove(b, slot) -> None:
+    _bcheck(_lib.lbm_batch_remove(b, int(slot)), b)
+
+
+def lbm_batch_members(b) -> int:
+    return int(_lib.lbm_batch_members(b))
+
+
+def lbm_batch_step(b, nsteps) -> None:
+    _bcheck(_lib.lbm_batch_step(b, int(nsteps)), b)
+
+
+def lbm_variant_count() -> int:
+    return int(_lib.lbm_variant_count())
+
+
+def lbm_batch_set_variant(b, variant) -> None:
+    _bcheck(_lib.lbm_batch_set_variant(b, int(variant)), b)
+
+
+def lbm_batch_variant(b) -> int:
+    return int(_lib.lbm_batch_variant(b))
+
+
+def lbm_batch_autotune(b, steps_per_variant=10):
+    """Returns (chosen variant, per-variant ms/step list)."""
+    n = lbm_variant_count()
+    ms = (ctypes.c_double * n)()
+    chosen = ctypes.c_int32()
+    _bcheck(_lib.lbm_batch_autotune(b, int(steps_per_variant),
+                                    ctypes.byref(chosen), ms), b)
+    return chosen.value, list(ms)
+
+
+def lbm_batch_destroy(b) -> None:
+    _lib.lbm_batch_destroy(b)
+
+
+class Batch:
+    """A batch of Domains stepped together (one launch per step); the
+    workspace comes from torch, the stream is shared with the members."""
+
+    def __init__(self, capacity, max_tiles, device="cuda", stream=None):
+        import torch
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        nbytes = lbm_batch_workspace_bytes(capacity, max_tiles)
+        if nbytes == 0:
+            raise LbmError(LBM_E_INVAL, "invalid batch size")
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.handle = lbm_batch_create(capacity, max_tiles,
+                                       self.workspace.data_ptr(), nbytes,
+                                       self.stream.cuda_stream)
+        self.members = {}
+
+    def add(self, dom):
+        slot = lbm_batch_add(self.handle, dom.ctx)
+        self.members[slot] = dom
+        return slot
+
+    def remove(self, slot):
+        lbm_batch_remove(self.handle, slot)
+        self.members.pop(slot, None)
+
+    def step(self, nsteps=1):
+        lbm_batch_step(self.handle, nsteps)
+
+    def set_variant(self, v):
+        lbm_batch_set_variant(self.handle, v)
+
+    def variant(self):
+        return lbm_batch_variant(self.handle)
+
+    def autotune(self, steps_per_variant=10):
+        return lbm_batch_autotune(self.handle, steps_per_variant)
+
+    def close(self):
+        if self.handle:
+            lbm_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Domain:

@@ -10,9 +10,11 @@
 #include <new>
 
 #include "../../include/lbmtau1.h"
+#include "lbm_ctx.h"
 #include "lbm_step.cuh"
 
 using lbmtau1::Fields;
+using lbmtau1::Layout;
 
 namespace {
 
@@ -22,17 +24,6 @@ constexpr int64_t kStagingNodes = 1 << 20;    // host-transfer chunk (nodes)
 constexpr int64_t kMaxExtent = int64_t(1) << 31;
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
-
-struct Layout {
-  int64_t pitch = 0, staging_rows = 0, nblocks = 0;
-  size_t field_bytes = 0;   // one field plane
-  size_t off_fields = 0;    // 6 planes: copy 0 (d, jx, jy), copy 1 (d, jx, jy)
-  size_t off_mask = 0;
-  size_t off_partials = 0;
-  size_t off_result = 0;    // 3 doubles + flag
-  size_t off_staging = 0;
-  size_t total = 0;
-};
 
 bool params_ok(const lbm_params *p) {
   return p && p->nx >= 1 && p->ny >= 1 && p->nx <= kMaxExtent &&
@@ -69,23 +60,6 @@ Layout make_layout(const lbm_params *p) {
 
 }  // namespace
 
-struct lbm_ctx {
-  lbm_params p;
-  Layout L;
-  char *base;
-  Fields f[2];
-  uint8_t *mask;
-  double *partials;
-  double *result;       // sum |du|^2, sum |u|^2, sum (rho - 1)
-  unsigned *flag;       // follows the three doubles
-  double *staging;
-  cudaStream_t stream;
-  int cur;              // copy holding the current state
-  bool has_geometry;
-  bool has_residual;
-  int64_t n_fluid;
-  char err[256];
-};
 
 namespace {
 

@@ -1,0 +1,43 @@
+// Internal definitions shared by the library's translation units: the
+// workspace layout and the context behind the opaque lbm_ctx handle.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/lbmtau1.h"
+#include "lbm_step.cuh"
+
+namespace lbmtau1 {
+
+struct Layout {
+  int64_t pitch = 0, staging_rows = 0, nblocks = 0;
+  size_t field_bytes = 0;   // one field plane
+  size_t off_fields = 0;    // 6 planes: copy 0 (d, jx, jy), copy 1 (d, jx, jy)
+  size_t off_mask = 0;
+  size_t off_partials = 0;
+  size_t off_result = 0;    // 3 doubles + flag
+  size_t off_staging = 0;
+  size_t total = 0;
+};
+
+}  // namespace lbmtau1
+
+struct lbm_ctx {
+  lbm_params p;
+  lbmtau1::Layout L;
+  char *base;
+  lbmtau1::Fields f[2];
+  uint8_t *mask;
+  double *partials;
+  double *result;       // sum |du|^2, sum |u|^2, sum (rho - 1)
+  unsigned *flag;       // follows the three doubles
+  double *staging;
+  cudaStream_t stream;
+  int cur;              // copy holding the current state
+  bool has_geometry;
+  bool has_residual;
+  int64_t n_fluid;
+  char err[256];
+};

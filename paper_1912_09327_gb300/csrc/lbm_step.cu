@@ -207,6 +207,11 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
                : "memory");
 }
 
+__device__ __forceinline__ void mbar_inval(uint64_t *bar) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
 // completes the current phase without data (a stage use that copies nothing)
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar))
@@ -301,24 +306,24 @@ __host__ __device__ constexpr int smem_bytes() {
   return 512 * static_cast<int>(sizeof(SolidSums)) + kWarps * ring_bytes<kC, kS>();
 }
 
-template <int kC, int kRows, int kMinBlocks, int kS, bool kReduce>
-__global__ void __launch_bounds__(kThreads, kMinBlocks)
-    lbm_step_kernel(const StepLaunch a) {
+// One block tile (bx, by) of a step: kWarps warp tiles of (30 kC) columns x
+// kRows rows stacked vertically.  `gx` is the number of tiles along x (for the
+// index of the block's reduction partial).  Every thread of the block calls it.
+template <int kC, int kRows, int kS, bool kReduce>
+__device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
+                                          int64_t by, int64_t gx,
+                                          const SolidSums *lut,
+                                          unsigned char *smem) {
   static_assert(kRows % 2 == 0, "rows per warp must be even");
-  static_assert(kS >= 4 && kS % 2 == 0 && kS <= 32, "ring stages");
+  static_assert(kS >= 4 && kS % 2 == 0 && kS <= 16, "ring stages");
   constexpr int kTile = (kLanes - 2) * kC;
   using St = Stage<kC>;
-  extern __shared__ __align__(128) unsigned char smem[];
-  SolidSums *lut = reinterpret_cast<SolidSums *>(smem);
-  build_solid_lut(lut);
-  __syncthreads();
 
   const int lane = threadIdx.x & (kLanes - 1);
   const int warp = threadIdx.x / kLanes;
-  const int64_t x0 = static_cast<int64_t>(blockIdx.x) * kTile;
+  const int64_t x0 = bx * kTile;
   const int64_t xb = x0 - kC + static_cast<int64_t>(kC) * lane;
-  const int64_t y0 =
-      (static_cast<int64_t>(blockIdx.y) * kWarps + warp) * kRows;
+  const int64_t y0 = (by * kWarps + warp) * kRows;
   const int64_t y1 = min(y0 + kRows, a.ny);
   const bool owner = lane >= 1 && lane <= kLanes - 2 && xb < a.nx;
   // interior tiles stream rows through the shared-memory ring
@@ -634,6 +639,12 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks)
         mbar_wait(bars + i % kS, static_cast<uint32_t>((i / kS) & 1));
       }
     }
+    if (bulk) {  // release the barriers so the ring can serve another tile
+      __syncwarp();
+      if (lane == 0)
+        for (int st = 0; st < kS; ++st) mbar_inval(bars + st);
+      __syncwarp();
+    }
   }
 
   if constexpr (kReduce) {
@@ -661,11 +672,79 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks)
       double s = 0.0;
 #pragma unroll
       for (int w = 0; w < kWarps; ++w) s += part[w][threadIdx.x];
-      const int64_t b =
-          static_cast<int64_t>(blockIdx.y) * gridDim.x + blockIdx.x;
+      const int64_t b = by * gx + bx;
       a.partials[3 * b + threadIdx.x] = s;
     }
   }
+}
+
+template <int kC, int kRows, int kMinBlocks, int kS, bool kReduce>
+__global__ void __launch_bounds__(kThreads, kMinBlocks)
+    lbm_step_kernel(const StepLaunch a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  SolidSums *lut = reinterpret_cast<SolidSums *>(smem);
+  build_solid_lut(lut);
+  __syncthreads();
+  step_tile<kC, kRows, kS, kReduce>(a, blockIdx.x, blockIdx.y, gridDim.x, lut,
+                                    smem);
+}
+
+// Batched step: a persistent grid takes block tiles of many domains from one
+// work list through an atomic counter, so that one launch advances every
+// member of a batch by one step.  Tile for tile it runs the same code as the
+// single-domain kernel, so each member's result does not depend on the batch.
+template <int kC, int kRows, int kMinBlocks, int kS, bool kReduce>
+__global__ void __launch_bounds__(kThreads, kMinBlocks)
+    lbm_batch_kernel(const BatchLaunch b) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  SolidSums *lut = reinterpret_cast<SolidSums *>(smem);
+  __shared__ int s_item;
+  build_solid_lut(lut);
+  __syncthreads();
+  const int n = *b.nitems;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = static_cast<int>(atomicAdd(b.counter, 1u));
+    __syncthreads();
+    const int it = s_item;
+    __syncthreads();
+    if (it >= n) break;
+    const int4 w = b.items[it];  // member, tile x, tile y
+    const BatchMember &m = b.members[w.x];
+    const int c = (m.cur ^ b.parity) & 1;
+    StepLaunch a;
+    a.src = m.f[c];
+    a.dst = m.f[1 - c];
+    a.mask = m.mask;
+    a.nx = m.nx;
+    a.ny = m.ny;
+    a.pitch = m.pitch;
+    a.periodic_x = m.periodic_x;
+    a.periodic_y = m.periodic_y;
+    a.fx = m.fx;
+    a.fy = m.fy;
+    a.partials = m.partials;
+    a.flag = m.flag;
+    step_tile<kC, kRows, kS, kReduce>(a, w.y, w.z, m.gx, lut, smem);
+  }
+}
+
+// One block per batch member: sums its block partials (fixed order) into its
+// result slot.
+__global__ void __launch_bounds__(256)
+    batch_finalize_kernel(const BatchMember *__restrict__ members) {
+  __shared__ double buf[3][256];
+  const BatchMember &m = members[blockIdx.x];
+  double s[3] = {0.0, 0.0, 0.0};
+  for (int64_t k = threadIdx.x; k < m.nblocks; k += 256)
+    for (int q = 0; q < 3; ++q) s[q] += m.partials[3 * k + q];
+  for (int q = 0; q < 3; ++q) buf[q][threadIdx.x] = s[q];
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+      for (int q = 0; q < 3; ++q) buf[q][threadIdx.x] += buf[q][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x < 3) m.result[threadIdx.x] = buf[threadIdx.x][0];
 }
 
 constexpr int kFinalizeThreads = 512;
@@ -764,6 +843,7 @@ cudaError_t launch_variant(const StepLaunch &a, dim3 g, cudaStream_t s) {
   static cudaError_t attr = cudaFuncSetAttribute(
       kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (attr != cudaSuccess) return attr;
+  (void)cudaGetLastError();  // an earlier, unrelated non-sticky error
   kern<<<g, kThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
@@ -783,6 +863,41 @@ int copy_grid(int64_t n) {
   return static_cast<int>(b < 4096 ? (b < 1 ? 1 : b) : 4096);
 }
 
+template <int kV, bool kReduce>
+cudaError_t launch_batch_variant(const BatchLaunch &b, cudaStream_t s) {
+  constexpr Variant v = kVariants[kV];
+  constexpr int smem = smem_bytes<v.cols, v.stages>();
+  auto kern = lbm_batch_kernel<v.cols, v.rows, v.min_blocks, v.stages, kReduce>;
+  // persistent grid: every resident block slot of the device, computed once
+  static int grid = [&] {
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             smem) != cudaSuccess)
+      return 0;
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads,
+                                                      smem) != cudaSuccess)
+      return 0;
+    return sms * (per_sm > 0 ? per_sm : 1);
+  }();
+  if (grid <= 0) return cudaErrorInvalidConfiguration;
+  (void)cudaGetLastError();
+  kern<<<grid, kThreads, smem, s>>>(b);
+  return cudaGetLastError();
+}
+
+template <bool kReduce>
+cudaError_t launch_batch_any(int v, const BatchLaunch &b, cudaStream_t s) {
+  switch (v) {
+    case 1: return launch_batch_variant<1, kReduce>(b, s);
+    case 2: return launch_batch_variant<2, kReduce>(b, s);
+    case 3: return launch_batch_variant<3, kReduce>(b, s);
+    default: return launch_batch_variant<0, kReduce>(b, s);
+  }
+}
+
 }  // namespace
 
 int64_t step_blocks(int64_t nx, int64_t ny) {
@@ -798,6 +913,31 @@ int64_t step_blocks(int64_t nx, int64_t ny) {
   return most;
 }
 
+int variant_count() { return kNumVariants; }
+
+void variant_tile(int v, int64_t *tile_x, int64_t *tile_y) {
+  const Variant t = kVariants[(v >= 0 && v < kNumVariants) ? v : 0];
+  *tile_x = (kLanes - 2) * t.cols;
+  *tile_y = static_cast<int64_t>(kWarps) * t.rows;
+}
+
+int default_variant() { return active_variant(); }
+
+cudaError_t launch_batch(int v, const BatchLaunch &b, bool reduce,
+                         cudaStream_t s) {
+  if (v < 0 || v >= kNumVariants) return cudaErrorInvalidValue;
+  return reduce ? launch_batch_any<true>(v, b, s)
+                : launch_batch_any<false>(v, b, s);
+}
+
+cudaError_t launch_batch_finalize(const BatchMember *members, int nmembers,
+                                  cudaStream_t s) {
+  if (nmembers <= 0) return cudaSuccess;
+  (void)cudaGetLastError();
+  batch_finalize_kernel<<<nmembers, 256, 0, s>>>(members);
+  return cudaGetLastError();
+}
+
 int64_t launched_blocks(int64_t nx, int64_t ny) {
   const dim3 g = step_grid(nx, ny);
   return static_cast<int64_t>(g.x) * g.y;
@@ -810,6 +950,7 @@ cudaError_t launch_step(const StepLaunch &a, bool reduce, cudaStream_t s) {
 
 cudaError_t launch_finalize(const double *partials, int64_t nblocks,
                             double *out, cudaStream_t s) {
+  (void)cudaGetLastError();
   finalize_kernel<<<1, kFinalizeThreads, 0, s>>>(partials, nblocks, out);
   return cudaGetLastError();
 }
@@ -817,6 +958,7 @@ cudaError_t launch_finalize(const double *partials, int64_t nblocks,
 cudaError_t launch_pack(const double *staging, Fields f, int64_t nx,
                         int64_t pitch, int64_t y0, int64_t rows,
                         cudaStream_t s) {
+  (void)cudaGetLastError();
   pack_kernel<<<copy_grid(nx * rows), 256, 0, s>>>(staging, f, nx, pitch, y0,
                                                    rows);
   return cudaGetLastError();
@@ -825,6 +967,7 @@ cudaError_t launch_pack(const double *staging, Fields f, int64_t nx,
 cudaError_t launch_unpack(Fields f, const uint8_t *mask, double *staging,
                           int64_t nx, int64_t pitch, int64_t y0, int64_t rows,
                           cudaStream_t s) {
+  (void)cudaGetLastError();
   unpack_kernel<<<copy_grid(nx * rows), 256, 0, s>>>(f, mask, staging, nx,
                                                      pitch, y0, rows);
   return cudaGetLastError();
@@ -832,6 +975,7 @@ cudaError_t launch_unpack(Fields f, const uint8_t *mask, double *staging,
 
 cudaError_t launch_solid_storage(Fields f, const uint8_t *mask, int64_t n,
                                  float fx, float fy, cudaStream_t s) {
+  (void)cudaGetLastError();
   solid_storage_kernel<<<copy_grid(n), 256, 0, s>>>(f, mask, n, fx, fy);
   return cudaGetLastError();
 }

@@ -25,6 +25,45 @@ struct StepLaunch {
   unsigned int *flag;   // sticky instability flag (reduced steps only)
 };
 
+// One member of a batch (see launch_batch): both field copies, the copy that
+// holds its current state, its node types and problem data, and its own
+// reduction partials and result slot.
+struct BatchMember {
+  Fields f[2];
+  const uint8_t *mask;
+  int64_t nx, ny, pitch;
+  int periodic_x, periodic_y;
+  float fx, fy;
+  double *partials;  // one triple per block tile
+  double *result;    // 3 doubles, then the flag word
+  unsigned int *flag;
+  int64_t gx;        // block tiles along x for the batch's tile variant
+  int64_t nblocks;   // block tiles of the member
+  int cur;           // copy holding the state when the batch step starts
+  int pad;
+};
+
+struct BatchLaunch {
+  const BatchMember *members;
+  const int4 *items;    // (member, tile x, tile y, 0)
+  const int *nitems;
+  unsigned int *counter;  // zeroed before the launch
+  int parity;             // step index within the call, mod 2
+};
+
+// Tile variants: their number, the block tile size of variant v, and the
+// default variant of the single-domain path.
+int variant_count();
+void variant_tile(int v, int64_t *tile_x, int64_t *tile_y);
+int default_variant();
+
+// Enqueues one batched step with tile variant v over a persistent grid; the
+// counter must have been zeroed on the stream before.
+cudaError_t launch_batch(int v, const BatchLaunch &b, bool reduce,
+                         cudaStream_t s);
+cudaError_t launch_batch_finalize(const BatchMember *members, int nmembers,
+                                  cudaStream_t s);
+
 // Upper bound on the thread blocks (reduction partials) of one step launch,
 // over every tile variant; and the count of the variant in use.
 int64_t step_blocks(int64_t nx, int64_t ny);

@@ -116,3 +116,30 @@ def test_status_strings(b):
                  "LBM_E_UNSTABLE", "LBM_E_STATE"]:
         assert b.lbm_status_string(getattr(b, name)) == name
     assert b.lbm_status_string(-99) == "LBM_E_UNKNOWN"
+
+
+def test_batch_arguments_checked_on_host(b):
+    lib = b._lib
+    assert b.lbm_batch_workspace_bytes(0, 10) == 0
+    assert b.lbm_batch_workspace_bytes(4, 0) == 0
+    need = b.lbm_batch_workspace_bytes(4, 100)
+    assert need > 0
+    out = ctypes.c_void_p()
+    assert lib.lbm_batch_create(4, 100, ctypes.c_void_p(4096 + 8), need, None,
+                                ctypes.byref(out)) == b.LBM_E_WORKSPACE
+    bt = b.lbm_batch_create(4, 100, 1 << 20, need)
+    try:
+        assert b.lbm_batch_members(bt) == 0
+        assert lib.lbm_batch_add(bt, None, None) == b.LBM_E_INVAL
+        p = b.make_params(20, 10)
+        ctx = b.lbm_create(p, 1 << 21, b.lbm_workspace_bytes(p))
+        # no geometry yet (and a different stream would also be refused)
+        assert lib.lbm_batch_add(bt, ctx, None) == b.LBM_E_STATE
+        b.lbm_destroy(ctx)
+        assert lib.lbm_batch_remove(bt, 0) == b.LBM_E_INVAL
+        assert lib.lbm_batch_set_variant(bt, b.lbm_variant_count()) == b.LBM_E_INVAL
+        assert lib.lbm_batch_step(bt, -1) == b.LBM_E_INVAL
+        assert lib.lbm_batch_step(bt, 3) == b.LBM_OK  # no members: no work
+        assert lib.lbm_batch_autotune(bt, 3, None, None) == b.LBM_E_INVAL
+    finally:
+        b.lbm_batch_destroy(bt)

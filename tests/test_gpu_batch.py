@@ -1,0 +1,147 @@
+"""Batched stepping (one launch per step for many domains) against stepping
+each domain alone and against the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1912_09327_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def b():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1912_09327_gb300 import binding
+    return binding
+
+
+def mixed_problems(count, seed=0, lo=20, hi=700):
+    """Seeded mix of channels, cavities, porous samples and random domains
+    with log-uniform side lengths."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        nx, ny = (int(round(v)) for v in np.exp(rng.uniform(np.log(lo), np.log(hi), 2)))
+        kind = i % 4
+        if kind == 0:
+            p = wl.channel(nx, max(ny, 5), 0.01)
+        elif kind == 1:
+            p = wl.cavity(nx, 0.1, ny=max(ny, 4))
+        elif kind == 2:
+            p = wl.porous(max(nx, 64), seed=i, r_min=3, r_max=8,
+                          ny=max(ny, 64), fx=1e-4)
+        else:
+            p = wl.random_problem(nx, ny, seed=i, periodic=(bool(i & 4), bool(i & 8)))
+        out.append(p)
+    return out
+
+
+def states(doms):
+    return [d.get_state() for d in doms]
+
+
+@pytest.mark.parametrize("nsteps", [1, 2, 37])
+def test_batch_equals_each_alone(b, nsteps):
+    probs = mixed_problems(10, seed=nsteps)
+    alone = []
+    for p in probs:
+        d = b.Domain.from_problem(p)
+        d.step(nsteps)
+        alone.append((d.get_state(), d.residual()))
+        d.close()
+    import torch
+    stream = torch.cuda.Stream()  # a capturable stream: graph chunks are used
+    doms = [b.Domain.from_problem(p, stream=stream) for p in probs]
+    batch = b.Batch(len(doms), 100000, stream=stream)
+    for d in doms:
+        batch.add(d)
+    batch.step(nsteps)
+    for d, (want, (res, mass)) in zip(doms, alone):
+        for x, y in zip(d.get_state(), want):
+            assert np.array_equal(x, y)
+        r2, m2 = d.residual()
+        assert r2 == pytest.approx(res, rel=1e-12, abs=1e-300)
+        assert m2 == pytest.approx(mass, rel=1e-12)
+    batch.close()
+
+
+def test_batch_variants_are_identical_and_autotune(b):
+    probs = mixed_problems(6, seed=11)
+    import torch
+    stream = torch.cuda.current_stream()
+    results = []
+    for v in range(b.lbm_variant_count()):
+        doms = [b.Domain.from_problem(p, stream=stream) for p in probs]
+        batch = b.Batch(len(doms), 100000, stream=stream)
+        for d in doms:
+            batch.add(d)
+        batch.set_variant(v)
+        batch.step(21)
+        results.append(states(doms))
+        batch.close()
+    for r in results[1:]:
+        for sa, sb in zip(results[0], r):
+            for x, y in zip(sa, sb):
+                assert np.array_equal(x, y)
+    # autotune: real steps, every variant timed, the fastest kept
+    doms = [b.Domain.from_problem(p, stream=stream) for p in probs]
+    batch = b.Batch(len(doms), 100000, stream=stream)
+    for d in doms:
+        batch.add(d)
+    chosen, ms = batch.autotune(4)
+    assert 0 <= chosen < b.lbm_variant_count()
+    assert all(t > 0 for t in ms) and ms[chosen] == min(ms)
+    ref = [b.Domain.from_problem(p, stream=stream) for p in probs]
+    for d in ref:
+        d.step((4 + 2) * b.lbm_variant_count())
+    for d, r in zip(doms, ref):
+        for x, y in zip(d.get_state(), r.get_state()):
+            assert np.array_equal(x, y)
+    batch.close()
+
+
+def test_batch_membership_changes(b):
+    probs = mixed_problems(5, seed=3)
+    import torch
+    stream = torch.cuda.current_stream()
+    doms = [b.Domain.from_problem(p, stream=stream) for p in probs]
+    batch = b.Batch(4, 100000, stream=stream)
+    slots = [batch.add(d) for d in doms[:4]]
+    with pytest.raises(b.LbmError):
+        batch.add(doms[4])            # full
+    batch.step(5)
+    batch.remove(slots[1])            # doms[1] leaves after 5 steps
+    batch.add(doms[4])                # doms[4] joins at 0 steps
+    batch.step(6)
+    counts = [11, 5, 11, 11, 6]
+    for d, p, n in zip(doms, probs, counts):
+        ref = b.Domain.from_problem(p, stream=stream)
+        ref.step(n)
+        for x, y in zip(d.get_state(), ref.get_state()):
+            assert np.array_equal(x, y)
+    batch.close()
+
+
+def test_batch_member_matches_oracle(b):
+    p = wl.random_problem(300, 170, seed=5, periodic=(True, False))
+    q = wl.cavity(257, 0.1, ny=133)
+    import torch
+    stream = torch.cuda.current_stream()
+    doms = [b.Domain.from_problem(x, stream=stream) for x in (p, q)]
+    batch = b.Batch(2, 10000, stream=stream)
+    for d in doms:
+        batch.add(d)
+    batch.step(20)
+    for d, x in zip(doms, (p, q)):
+        o = oracle.run(x.mask, *x.state(), 20, x.periodic, x.force)
+        g = d.moments()
+        fluid = x.mask != wl.SOLID
+        amp = max(np.abs(x.rho - 1).max(), np.abs(x.jx).max(), 1e-3)
+        for a_, b_ in zip(g, o):
+            assert np.abs(a_ - b_)[fluid].max() <= 2e-6 * amp * np.sqrt(20) + 1e-9
+    batch.close()
