@@ -53,6 +53,11 @@ def parse_args(argv=None):
     ap.add_argument("--size", type=int, default=16384)
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--batched-domains", type=int, default=512)
+    ap.add_argument("--batched-steps", type=int, default=2000)
+    ap.add_argument("--serving-requests", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args(argv)
 
@@ -253,6 +258,84 @@ def run_e2e(binding, dom, n, steps):
             "api": "lbm_set_state + lbm_step(1) + lbm_get_state + lbm_residual, pinned host"}
 
 
+def run_batched(binding, domains, steps, plain_steps=200):
+    """Configuration: 512 independent domains (seeded thirds of channels,
+    cavities and porous samples, sides log-uniform in [64, 1024]), 2000 steps
+    each, FP32; batched (one launch per step for all domains, autotuned tile
+    variant) against the plain form (one domain after another, lbm_step)."""
+    import torch
+    from paper_1912_09327_gb300 import workloads as wl
+    probs = wl.batch_mix(domains, seed=0)
+    nodes = sum(p.mask.size for p in probs)
+    stream = torch.cuda.Stream()
+    doms = [binding.Domain.from_problem(p, stream=stream) for p in probs]
+    tiles = 0
+    for p in probs:
+        ny, nx = p.mask.shape
+        tiles += ((nx + 59) // 60) * ((ny + 127) // 128)  # bound over variants
+    batch = binding.Batch(len(doms), tiles, stream=stream)
+    for d in doms:
+        batch.add(d)
+    chosen, tuned = batch.autotune(10)
+    stream.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    batch.step(steps)
+    e1.record(stream)
+    batch.residuals()  # syncs; every member's residual of the last step
+    t_batch = e0.elapsed_time(e1) / 1e3
+    batch.close()
+    for d in doms:
+        d.close()
+    torch.cuda.empty_cache()
+    # the plain form, one domain after another, timed over plain_steps of the
+    # steps (its time per step does not depend on the step) and scaled
+    doms = [binding.Domain.from_problem(p, stream=stream) for p in probs]
+    stream.synchronize()
+    e0.record(stream)
+    for d in doms:
+        d.step(plain_steps)
+    e1.record(stream)
+    stream.synchronize()
+    t_plain = e0.elapsed_time(e1) / 1e3 * steps / plain_steps
+    for d in doms:
+        d.close()
+    torch.cuda.empty_cache()
+    return {"workload": "%d domains (channel/cavity/porous thirds, sides "
+                        "log-uniform 64..1024), %d steps each, FP32"
+                        % (domains, steps),
+            "nodes": int(nodes), "variant": chosen,
+            "autotune_ms_per_step": [round(t, 4) for t in tuned],
+            "batched_s": round(t_batch, 4), "plain_s": round(t_plain, 4),
+            "plain_timed_steps": plain_steps,
+            "solves_per_s_batched": round(domains / t_batch, 2),
+            "solves_per_s_plain": round(domains / t_plain, 2),
+            "mlups_batched": round(nodes * steps / t_batch / 1e6, 1),
+            "mlups_plain": round(nodes * steps / t_plain / 1e6, 1),
+            "speedup": round(t_plain / t_batch, 2)}
+
+
+def run_serving(requests_n, cap=10000):
+    """Configuration: Poisson arrivals (seeded, 200 requests/s) of channel,
+    cavity and porous solves with sides log-uniform in [64, 2048], each run to
+    residual 1e-7 (capped at `cap` steps, reported), admitted by free device
+    memory; continuous batching against the plain sequential form."""
+    from paper_1912_09327_gb300 import serving, workloads as wl
+    reqs = wl.request_stream(requests_n, rate=200.0, seed=0)
+    srv = serving.Server(capacity=max(requests_n, 8), chunk=200,
+                         residual_tol=1e-7, max_steps=cap)
+    batched = serving.summary(srv.run(reqs))
+    srv.close()
+    plain = serving.summary(serving.serve_sequential(reqs, chunk=200,
+                                                     residual_tol=1e-7,
+                                                     max_steps=cap))
+    return {"workload": "%d requests, Poisson 200/s, sides log-uniform "
+                        "64..2048, residual 1e-7, cap %d steps, chunk 200"
+                        % (requests_n, cap),
+            "continuous_batching": batched, "plain_sequential": plain}
+
+
 def cpu_baseline(size, rows=1024, seconds=10.0):
     """The FP64 oracle as it stands, on all host cores, on a bounded sample:
     whole steps over the top `rows` rows of the size x size cavity (full
@@ -417,6 +500,11 @@ def main(argv=None):
     if rank == 0 and not args.no_sweep:
         line["sweep"] = run_sweep(binding, stream,
                                   [256, 512, 1024, 2048, 4096, 8192, 16384])
+    if rank == 0 and not args.no_batched:
+        line["batched"] = run_batched(binding, args.batched_domains,
+                                      args.batched_steps)
+    if rank == 0 and not args.no_serving:
+        line["serving"] = run_serving(args.serving_requests)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(n)
     if rank == 0:

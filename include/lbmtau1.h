@@ -258,6 +258,14 @@ int32_t lbm_batch_variant(const lbm_batch *b);
 int lbm_batch_autotune(lbm_batch *b, int32_t steps_per_variant,
                        int32_t *chosen, double *ms_per_step);
 
+/* Residual and mass of every member's last step (as lbm_residual), by slot,
+ * read with one device-to-host copy: residual, mass and status are host
+ * arrays of the batch capacity; status[slot] is LBM_OK, LBM_E_UNSTABLE,
+ * LBM_E_CUDA (copy timeout) or LBM_E_STATE (empty slot / no step yet).
+ * Synchronises the stream.  Errors: LBM_E_INVAL, LBM_E_CUDA. */
+int lbm_batch_residuals(lbm_batch *b, double *residual, double *mass,
+                        int32_t *status);
+
 /* Frees the batch's host state (members and workspace stay the caller's). */
 void lbm_batch_destroy(lbm_batch *b);
 

@@ -86,6 +86,8 @@ _lib.lbm_batch_variant.restype = ctypes.c_int32
 _lib.lbm_batch_autotune.argtypes = [_vp, ctypes.c_int32,
                                     ctypes.POINTER(ctypes.c_int32), _vp]
 _lib.lbm_batch_autotune.restype = ctypes.c_int
+_lib.lbm_batch_residuals.argtypes = [_vp, _vp, _vp, _vp]
+_lib.lbm_batch_residuals.restype = ctypes.c_int
 _lib.lbm_batch_destroy.argtypes = [_vp]
 _lib.lbm_batch_destroy.restype = None
 _lib.lbm_batch_last_error.argtypes = [_vp]
@@ -272,6 +274,17 @@ def lbm_batch_autotune(b, steps_per_variant=10):
     return chosen.value, list(ms)
 
 
+def lbm_batch_residuals(b, capacity):
+    """(residual, mass, status) arrays indexed by slot."""
+    res = np.zeros(capacity, np.float64)
+    mass = np.zeros(capacity, np.float64)
+    st = np.zeros(capacity, np.int32)
+    _bcheck(_lib.lbm_batch_residuals(b, _vp(res.ctypes.data),
+                                     _vp(mass.ctypes.data),
+                                     _vp(st.ctypes.data)), b)
+    return res, mass, st
+
+
 def lbm_batch_destroy(b) -> None:
     _lib.lbm_batch_destroy(b)
 
@@ -282,6 +295,7 @@ class Batch:
 
     def __init__(self, capacity, max_tiles, device="cuda", stream=None):
         import torch
+        self.capacity = int(capacity)
         self.device = torch.device(device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         nbytes = lbm_batch_workspace_bytes(capacity, max_tiles)
@@ -313,6 +327,9 @@ class Batch:
 
     def autotune(self, steps_per_variant=10):
         return lbm_batch_autotune(self.handle, steps_per_variant)
+
+    def residuals(self):
+        return lbm_batch_residuals(self.handle, self.capacity)
 
     def close(self):
         if self.handle:

@@ -10,6 +10,7 @@
 // graph of kChunk steps.  Each tile runs the same code as the single-domain
 // kernel, so a member's state is bit for bit the one it would reach alone.
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
@@ -33,6 +34,7 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 struct BatchLayout {
   size_t off_members = 0, off_items = 0, off_nitems = 0, off_counters = 0;
+  size_t off_gather = 0;
   size_t total = 0;
 };
 
@@ -47,6 +49,8 @@ BatchLayout batch_layout(int32_t capacity, int64_t max_tiles) {
   off += kAlign;
   L.off_counters = off;
   off += align_up(sizeof(unsigned) * (kChunk + 1), kAlign);
+  L.off_gather = off;
+  off += align_up(sizeof(double) * 4 * static_cast<size_t>(capacity), kAlign);
   L.total = off;
   return L;
 }
@@ -60,6 +64,7 @@ struct lbm_batch {
   int4 *d_items;
   int *d_nitems;
   unsigned *d_counters;  // [0, kChunk) graph steps, [kChunk] direct steps
+  double *d_gather;      // 4 doubles per member: result sums and flag
   cudaStream_t stream;
   std::vector<lbm_ctx *> slots;
   std::vector<BatchMember> h_members;
@@ -260,6 +265,7 @@ int lbm_batch_create(int32_t capacity, int64_t max_tiles, void *dev_workspace,
   b->d_items = reinterpret_cast<int4 *>(base + L.off_items);
   b->d_nitems = reinterpret_cast<int *>(base + L.off_nitems);
   b->d_counters = reinterpret_cast<unsigned *>(base + L.off_counters);
+  b->d_gather = reinterpret_cast<double *>(base + L.off_gather);
   b->stream = static_cast<cudaStream_t>(cuda_stream);
   b->slots.assign(capacity, nullptr);
   b->nitems = 0;
@@ -399,6 +405,46 @@ int lbm_batch_autotune(lbm_batch *b, int32_t steps_per_variant,
   st = lbm_batch_set_variant(b, best);
   if (chosen) *chosen = best;
   return st;
+}
+
+int lbm_batch_residuals(lbm_batch *b, double *residual, double *mass,
+                        int32_t *status) {
+  if (!b) return LBM_E_INVAL;
+  if (!residual || !mass || !status)
+    return bfail(b, LBM_E_INVAL, "null output array");
+  for (int32_t i = 0; i < b->capacity; ++i) {
+    residual[i] = mass[i] = 0.0;
+    status[i] = LBM_E_STATE;
+  }
+  int st = upload(b);  // descriptors in slot order of the current members
+  if (st) return st;
+  const int n = static_cast<int>(b->packed.size());
+  if (n == 0) return LBM_OK;
+  cudaError_t e = lbmtau1::launch_batch_gather(b->d_members, n, b->d_gather,
+                                               b->stream);
+  if (e != cudaSuccess) return bcuda(b, e, "gather kernel");
+  std::vector<double> h(4 * static_cast<size_t>(n));
+  e = cudaMemcpyAsync(h.data(), b->d_gather, sizeof(double) * h.size(),
+                      cudaMemcpyDeviceToHost, b->stream);
+  if (e != cudaSuccess) return bcuda(b, e, "cudaMemcpyAsync(gather)");
+  e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return bcuda(b, e, "cudaStreamSynchronize");
+  int k = 0;
+  for (int32_t i = 0; i < b->capacity; ++i) {
+    lbm_ctx *c = b->slots[i];
+    if (!c) continue;
+    const double *r = &h[4 * static_cast<size_t>(k++)];
+    unsigned flag;
+    memcpy(&flag, &r[3], sizeof flag);
+    residual[i] = r[1] > 0.0 ? sqrt(r[0] / r[1]) : sqrt(r[0]);
+    mass[i] = static_cast<double>(c->n_fluid) + r[2];
+    status[i] = !c->has_residual ? LBM_E_STATE
+                : (flag & 2u)    ? LBM_E_CUDA
+                : (flag & 1u)    ? LBM_E_UNSTABLE
+                                 : LBM_OK;
+  }
+  b->err[0] = '\0';
+  return LBM_OK;
 }
 
 void lbm_batch_destroy(lbm_batch *b) {

@@ -728,6 +728,15 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks)
   }
 }
 
+// Copies every member's result slot (3 sums and the flag word) into out,
+// 4 doubles per member in descriptor order.
+__global__ void batch_gather_kernel(const BatchMember *__restrict__ members,
+                                    int nmembers, double *__restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nmembers)
+    for (int q = 0; q < 4; ++q) out[4 * i + q] = members[i].result[q];
+}
+
 // One block per batch member: sums its block partials (fixed order) into its
 // result slot.
 __global__ void __launch_bounds__(256)
@@ -935,6 +944,15 @@ cudaError_t launch_batch_finalize(const BatchMember *members, int nmembers,
   if (nmembers <= 0) return cudaSuccess;
   (void)cudaGetLastError();
   batch_finalize_kernel<<<nmembers, 256, 0, s>>>(members);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_gather(const BatchMember *members, int nmembers,
+                                double *out, cudaStream_t s) {
+  if (nmembers <= 0) return cudaSuccess;
+  (void)cudaGetLastError();
+  batch_gather_kernel<<<(nmembers + 127) / 128, 128, 0, s>>>(members, nmembers,
+                                                             out);
   return cudaGetLastError();
 }
 

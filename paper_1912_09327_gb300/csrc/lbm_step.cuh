@@ -63,6 +63,10 @@ cudaError_t launch_batch(int v, const BatchLaunch &b, bool reduce,
                          cudaStream_t s);
 cudaError_t launch_batch_finalize(const BatchMember *members, int nmembers,
                                   cudaStream_t s);
+// Gathers each member's 3 result sums and flag word into out (4 doubles per
+// member, descriptor order).
+cudaError_t launch_batch_gather(const BatchMember *members, int nmembers,
+                                double *out, cudaStream_t s);
 
 // Upper bound on the thread blocks (reduction partials) of one step launch,
 // over every tile variant; and the count of the variant in use.

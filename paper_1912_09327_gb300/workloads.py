@@ -150,3 +150,67 @@ def random_problem(nx: int, ny: int, seed: int = 0, p_solid: float = 0.2,
     solid = mask == SOLID
     r[solid], u[solid], v[solid] = 1.0, 0.0, 0.0
     return Problem("random", mask, tuple(periodic), tuple(force), r, u, v)
+
+
+def _log_uniform_side(rng, lo, hi):
+    return int(round(float(np.exp(rng.uniform(np.log(lo), np.log(hi))))))
+
+
+def mixed_domain(kind: str, nx: int, ny: int, seed: int = 0) -> Problem:
+    """One domain of the batch and serving mixes: a channel (u_max 0.01), a
+    lid-driven cavity (lid 0.1) or a periodic porous sample with disc radii
+    scaled to the domain (8..24 nodes at 512 nodes across, at least 2..3)."""
+    if kind == "channel":
+        return channel(nx, max(ny, 5), 0.01)
+    if kind == "cavity":
+        return cavity(nx, 0.1, ny=max(ny, 4))
+    side = min(nx, ny)
+    r_min = max(2, int(round(8 * side / 512)))
+    r_max = max(r_min + 1, int(round(24 * side / 512)))
+    return porous(nx, seed=seed, r_min=r_min, r_max=r_max, ny=ny, fx=1e-5)
+
+
+KINDS = ("channel", "cavity", "porous")
+
+
+def batch_mix(count: int = 512, seed: int = 0, lo: int = 64, hi: int = 1024):
+    """The batched workload: a seeded mix of channels, cavities and porous
+    samples in equal thirds, side lengths log-uniform in [lo, hi] with nx and
+    ny drawn independently."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        nx = _log_uniform_side(rng, lo, hi)
+        ny = _log_uniform_side(rng, lo, hi)
+        out.append(mixed_domain(KINDS[i % 3], nx, ny, seed=seed * 100003 + i))
+    return out
+
+
+@dataclass
+class Request:
+    rid: int
+    arrival: float        # seconds after the start of the run
+    kind: str
+    nx: int
+    ny: int
+    seed: int
+
+    def problem(self) -> Problem:
+        return mixed_domain(self.kind, self.nx, self.ny, self.seed)
+
+
+def request_stream(count: int, rate: float = 200.0, seed: int = 0,
+                   lo: int = 64, hi: int = 2048):
+    """Poisson arrivals at `rate` requests per second (exponential gaps),
+    kinds drawn uniformly from the three mixes, sides log-uniform in
+    [lo, hi]."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for i in range(count):
+        t += float(rng.exponential(1.0 / rate))
+        kind = KINDS[int(rng.integers(0, 3))]
+        nx = _log_uniform_side(rng, lo, hi)
+        ny = _log_uniform_side(rng, lo, hi)
+        out.append(Request(i, t, kind, nx, ny, seed * 100003 + i))
+    return out
