@@ -56,8 +56,12 @@ extern "C" {
 #define LBM_SOLID 1
 #define LBM_FIXED 2
 
-/* Device storage formats. */
-#define LBM_STORAGE_F32 0 /* rho - 1, jx, jy as float32 (24 B/node, 2 copies) */
+/* Device storage formats.  Arithmetic is FP32 in all of them, and the
+ * residual and mass reductions FP64. */
+#define LBM_STORAGE_F32 0  /* rho - 1, jx, jy as float32 (24 B/node, 2 copies) */
+#define LBM_STORAGE_F16 1  /* as IEEE binary16, (rho - 1) * 2^10 and j * 2^6
+                              (12 B/node, 2 copies) */
+#define LBM_STORAGE_BF16 2 /* as bfloat16, unscaled (12 B/node, 2 copies) */
 
 /* Problem statement.  Zero-initialise before filling in. */
 typedef struct lbm_params {
@@ -67,7 +71,7 @@ typedef struct lbm_params {
   int32_t periodic_y; /* nonzero: y wraps */
   double fx;          /* body force, momentum added per node per step */
   double fy;
-  int32_t storage;    /* LBM_STORAGE_F32 */
+  int32_t storage;    /* LBM_STORAGE_F32, _F16 or _BF16 */
   int32_t reserved;   /* must be 0 */
 } lbm_params;
 
@@ -134,7 +138,8 @@ int lbm_moments(lbm_ctx *ctx, double *rho, double *jx, double *jy);
 /*
  * Exact state transfer in the device storage format, for checkpoint/resume:
  * three caller-owned host arrays of nx*ny elements (float for
- * LBM_STORAGE_F32) holding rho - 1, jx and jy exactly as stored (solid
+ * LBM_STORAGE_F32, 16-bit words for _F16 and _BF16, scaled as stated above)
+ * holding rho - 1, jx and jy exactly as stored (solid
  * nodes: 0, -fx, -fy; lbm_set_state writes those there whatever it is
  * given).  A state saved with lbm_get_state and loaded with lbm_set_state
  * into a context with the same parameters and geometry continues bit for bit.  lbm_get_state
@@ -228,9 +233,9 @@ int lbm_batch_create(int32_t capacity, int64_t max_tiles, void *dev_workspace,
                      size_t workspace_bytes, void *cuda_stream,
                      lbm_batch **out);
 
-/* Adds a context (same stream as the batch, geometry set) and returns its
- * slot; the context must outlive its membership.  Errors: LBM_E_INVAL,
- * LBM_E_STATE, LBM_E_WORKSPACE (batch full). */
+/* Adds a context (same stream and storage format as the other members,
+ * geometry set) and returns its slot; the context must outlive its
+ * membership.  Errors: LBM_E_INVAL, LBM_E_STATE, LBM_E_WORKSPACE (full). */
 int lbm_batch_add(lbm_batch *b, lbm_ctx *ctx, int32_t *slot);
 
 /* Removes the member in `slot` (between steps).  Errors: LBM_E_INVAL. */

@@ -23,6 +23,13 @@ LBM_E_UNSTABLE = -4
 LBM_E_STATE = -5
 LBM_FLUID, LBM_SOLID, LBM_FIXED = 0, 1, 2
 LBM_STORAGE_F32 = 0
+LBM_STORAGE_F16 = 1
+LBM_STORAGE_BF16 = 2
+STORAGE_NAMES = {"f32": LBM_STORAGE_F32, "f16": LBM_STORAGE_F16,
+                 "bf16": LBM_STORAGE_BF16}
+# host dtype of the exact state transfers (bfloat16 as raw 16-bit words)
+STATE_DTYPE = {LBM_STORAGE_F32: np.float32, LBM_STORAGE_F16: np.float16,
+               LBM_STORAGE_BF16: np.uint16}
 
 LIB_PATH = _build.LIB
 if not os.path.exists(LIB_PATH):
@@ -175,17 +182,15 @@ def lbm_moments(ctx, rho, jx, jy) -> None:
 
 
 def lbm_get_state(ctx, drho, jx, jy) -> None:
-    """Fills host float32 buffers with the stored rho - 1, jx, jy."""
-    for a in (drho, jx, jy):
-        if isinstance(a, np.ndarray) and a.dtype != np.float32:
-            raise TypeError("state buffers must be float32")
+    """Fills host buffers with the stored rho - 1, jx, jy (storage format;
+    the caller's arrays must have its element size)."""
     _check(_lib.lbm_get_state(ctx, *[_vp(_ptr(a)) for a in (drho, jx, jy)]), ctx)
 
 
 def lbm_set_state(ctx, drho, jx, jy) -> None:
-    """Loads host float32 rho - 1, jx, jy exactly."""
-    arrs = [np.ascontiguousarray(a, dtype=np.float32)
-            if isinstance(a, np.ndarray) else a for a in (drho, jx, jy)]
+    """Loads rho - 1, jx, jy in the storage format exactly."""
+    arrs = [np.ascontiguousarray(a) if isinstance(a, np.ndarray) else a
+            for a in (drho, jx, jy)]
     _check(_lib.lbm_set_state(ctx, *[_vp(_ptr(a)) for a in arrs]), ctx)
 
 
@@ -348,10 +353,13 @@ class Domain:
     a context.  Methods map one-to-one to the C calls."""
 
     def __init__(self, nx, ny, periodic=(False, False), force=(0.0, 0.0),
-                 device="cuda", stream=None):
+                 device="cuda", stream=None, storage=LBM_STORAGE_F32):
         import torch
         self.nx, self.ny = int(nx), int(ny)
-        self.params = make_params(nx, ny, periodic, force)
+        if isinstance(storage, str):
+            storage = STORAGE_NAMES[storage]
+        self.storage = int(storage)
+        self.params = make_params(nx, ny, periodic, force, self.storage)
         nbytes = lbm_workspace_bytes(self.params)
         if nbytes == 0:
             raise LbmError(LBM_E_INVAL, "invalid domain parameters")
@@ -386,7 +394,8 @@ class Domain:
 
     def get_state(self, out=None):
         if out is None:
-            out = tuple(np.empty((self.ny, self.nx), np.float32) for _ in range(3))
+            dt = STATE_DTYPE[self.storage]
+            out = tuple(np.empty((self.ny, self.nx), dt) for _ in range(3))
         lbm_get_state(self.ctx, *out)
         return out
 

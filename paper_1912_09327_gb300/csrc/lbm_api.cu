@@ -27,7 +27,9 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 bool params_ok(const lbm_params *p) {
   return p && p->nx >= 1 && p->ny >= 1 && p->nx <= kMaxExtent &&
-         p->ny <= kMaxExtent && p->storage == LBM_STORAGE_F32 &&
+         p->ny <= kMaxExtent &&
+         (p->storage == LBM_STORAGE_F32 || p->storage == LBM_STORAGE_F16 ||
+          p->storage == LBM_STORAGE_BF16) &&
          p->reserved == 0 && isfinite(p->fx) && isfinite(p->fy);
 }
 
@@ -35,7 +37,8 @@ Layout make_layout(const lbm_params *p) {
   Layout L;
   L.pitch = (p->nx + kPitchAlign - 1) / kPitchAlign * kPitchAlign;
   const size_t plane = static_cast<size_t>(L.pitch) * p->ny;
-  L.field_bytes = align_up(plane * sizeof(float), kAlign);
+  L.field_bytes =
+      align_up(plane * lbmtau1::storage_bytes(p->storage), kAlign);
   L.nblocks = lbmtau1::step_blocks(p->nx, p->ny);
   int64_t rows = kStagingNodes / p->nx;
   if (rows < 1) rows = 1;
@@ -97,7 +100,7 @@ int bind_device(lbm_ctx *c) {
 int apply_solid_storage(lbm_ctx *c, int copy) {
   const int64_t n = c->L.pitch * c->p.ny;
   cudaError_t e = lbmtau1::launch_solid_storage(
-      c->f[copy], c->mask, n, static_cast<float>(c->p.fx),
+      c->p.storage, c->f[copy], c->mask, n, static_cast<float>(c->p.fx),
       static_cast<float>(c->p.fy), c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "solid storage kernel");
   return LBM_OK;
@@ -213,8 +216,9 @@ int lbm_set_moments(lbm_ctx *c, const double *rho, const double *jx,
                                       cudaMemcpyHostToDevice, c->stream);
       if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpyAsync(H2D)");
     }
-    cudaError_t e = lbmtau1::launch_pack(c->staging, c->f[c->cur], nx,
-                                         c->L.pitch, y0, rows, c->stream);
+    cudaError_t e = lbmtau1::launch_pack(c->p.storage, c->staging,
+                                         c->f[c->cur], nx, c->L.pitch, y0,
+                                         rows, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "pack kernel");
   }
   st = apply_solid_storage(c, c->cur);
@@ -236,10 +240,11 @@ int lbm_set_state(lbm_ctx *c, const void *drho, const void *jx,
   int st = bind_device(c);
   if (st) return st;
   const void *src[3] = {drho, jx, jy};
-  float *dst[3] = {c->f[c->cur].d, c->f[c->cur].jx, c->f[c->cur].jy};
-  const size_t row = static_cast<size_t>(c->p.nx) * sizeof(float);
+  void *dst[3] = {c->f[c->cur].d, c->f[c->cur].jx, c->f[c->cur].jy};
+  const size_t es = lbmtau1::storage_bytes(c->p.storage);
+  const size_t row = static_cast<size_t>(c->p.nx) * es;
   for (int k = 0; k < 3; ++k) {
-    cudaError_t e = cudaMemcpy2DAsync(dst[k], c->L.pitch * sizeof(float),
+    cudaError_t e = cudaMemcpy2DAsync(dst[k], c->L.pitch * es,
                                       src[k], row, row, c->p.ny,
                                       cudaMemcpyHostToDevice, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpy2DAsync(H2D)");
@@ -262,11 +267,12 @@ int lbm_get_state(lbm_ctx *c, void *drho, void *jx, void *jy) {
   int st = bind_device(c);
   if (st) return st;
   void *dst[3] = {drho, jx, jy};
-  const float *src[3] = {c->f[c->cur].d, c->f[c->cur].jx, c->f[c->cur].jy};
-  const size_t row = static_cast<size_t>(c->p.nx) * sizeof(float);
+  const void *src[3] = {c->f[c->cur].d, c->f[c->cur].jx, c->f[c->cur].jy};
+  const size_t es = lbmtau1::storage_bytes(c->p.storage);
+  const size_t row = static_cast<size_t>(c->p.nx) * es;
   for (int k = 0; k < 3; ++k) {
-    cudaError_t e = cudaMemcpy2DAsync(dst[k], row, src[k],
-                                      c->L.pitch * sizeof(float), row,
+    cudaError_t e = cudaMemcpy2DAsync(dst[k], row, src[k], c->L.pitch * es,
+                                      row,
                                       c->p.ny, cudaMemcpyDeviceToHost,
                                       c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpy2DAsync(D2H)");
@@ -294,6 +300,7 @@ int lbm_step(lbm_ctx *c, int64_t nsteps) {
   a.fy = static_cast<float>(c->p.fy);
   a.partials = c->partials;
   a.flag = c->flag;
+  a.storage = c->p.storage;
   for (int64_t s = 0; s < nsteps; ++s) {
     a.src = c->f[c->cur];
     a.dst = c->f[1 - c->cur];
@@ -321,8 +328,9 @@ int lbm_moments(lbm_ctx *c, double *rho, double *jx, double *jy) {
     const int64_t rows =
         y0 + c->L.staging_rows <= c->p.ny ? c->L.staging_rows : c->p.ny - y0;
     const size_t n = static_cast<size_t>(rows) * nx;
-    cudaError_t e = lbmtau1::launch_unpack(c->f[c->cur], c->mask, c->staging,
-                                           nx, c->L.pitch, y0, rows, c->stream);
+    cudaError_t e = lbmtau1::launch_unpack(c->p.storage, c->f[c->cur],
+                                           c->mask, c->staging, nx, c->L.pitch,
+                                           y0, rows, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "unpack kernel");
     double *dst[3] = {rho, jx, jy};
     for (int k = 0; k < 3; ++k) {

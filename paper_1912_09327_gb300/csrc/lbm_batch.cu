@@ -72,6 +72,7 @@ struct lbm_batch {
   std::vector<lbm_ctx *> packed;  // members in descriptor order
   int nitems;
   int variant;
+  int storage;  // storage format of the members (-1 while empty)
   bool items_dirty;
   cudaGraphExec_t graph;
   int graph_variant;
@@ -174,6 +175,7 @@ BatchLaunch launch_args(lbm_batch *b, unsigned *counter, int parity) {
   L.nitems = b->d_nitems;
   L.counter = counter;
   L.parity = parity;
+  L.storage = b->storage;
   return L;
 }
 
@@ -269,6 +271,7 @@ int lbm_batch_create(int32_t capacity, int64_t max_tiles, void *dev_workspace,
   b->stream = static_cast<cudaStream_t>(cuda_stream);
   b->slots.assign(capacity, nullptr);
   b->nitems = 0;
+  b->storage = -1;
   b->variant = lbmtau1::default_variant();
   b->items_dirty = true;
   b->graph = nullptr;
@@ -287,11 +290,14 @@ int lbm_batch_add(lbm_batch *b, lbm_ctx *ctx, int32_t *slot) {
     return bfail(b, LBM_E_INVAL, "member must use the batch's stream");
   if (!ctx->has_geometry)
     return bfail(b, LBM_E_STATE, "member has no geometry");
+  if (lbm_batch_members(b) > 0 && ctx->p.storage != b->storage)
+    return bfail(b, LBM_E_INVAL, "members must share one storage format");
   for (lbm_ctx *c : b->slots)
     if (c == ctx) return bfail(b, LBM_E_INVAL, "context already a member");
   for (int32_t i = 0; i < b->capacity; ++i)
     if (!b->slots[i]) {
       b->slots[i] = ctx;
+      b->storage = ctx->p.storage;
       b->items_dirty = true;
       if (slot) *slot = i;
       b->err[0] = '\0';

@@ -39,9 +39,13 @@
 // On the last step of an lbm_step call the same kernel also reduces
 // sum |du|^2, sum |u|^2 and sum delta (warp shuffles, FP64 block partials) and
 // raises a sticky flag on rho <= 0 or non-finite values.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <float.h>
 #include <stdint.h>
 #include <stdlib.h>
+
+#include <type_traits>
 
 #include "lbm_step.cuh"
 
@@ -84,25 +88,69 @@ __device__ __forceinline__ float2 sub(float2 a, float2 b) {
   return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
 }
 
-// Loads kC consecutive floats (one vector) of row `row` at column xb.
-template <int kC>
-__device__ __forceinline__ void load_vec(const float *p, float (&o)[kC]) {
-  if constexpr (kC == 4) {
-    const float4 v = __ldg(reinterpret_cast<const float4 *>(p));
-    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
-  } else {
-    const float2 v = __ldg(reinterpret_cast<const float2 *>(p));
-    o[0] = v.x; o[1] = v.y;
+// Storage formats.  All arithmetic is FP32; a 16-bit format stores the
+// deviations rho - 1 and j scaled by exact powers of two (FP16: 2^10 and 2^6,
+// which keep typical values, |rho - 1| >= 1e-7 and |j| >= 1e-6, out of the
+// subnormal range; BF16 has FP32's exponent range and needs none).
+template <typename T>
+struct Storage;
+template <>
+struct Storage<float> {
+  static constexpr float kD = 1.0f, kJ = 1.0f;
+  __device__ static float decode(float v) { return v; }
+  __device__ static float encode(float v) { return v; }
+};
+template <>
+struct Storage<__half> {
+  static constexpr float kD = 1024.0f, kJ = 64.0f;
+  __device__ static float decode(__half v) { return __half2float(v); }
+  __device__ static __half encode(float v) { return __float2half_rn(v); }
+};
+template <>
+struct Storage<__nv_bfloat16> {
+  static constexpr float kD = 1.0f, kJ = 1.0f;
+  __device__ static float decode(__nv_bfloat16 v) { return __bfloat162float(v); }
+  __device__ static __nv_bfloat16 encode(float v) {
+    return __float2bfloat16_rn(v);
   }
+};
+
+// kC consecutive elements as one vector load / store.
+template <int kC, typename T>
+struct Vec {
+  static constexpr int kBytes = kC * static_cast<int>(sizeof(T));
+  using type = typename std::conditional<
+      kBytes == 16, uint4,
+      typename std::conditional<kBytes == 8, uint2, unsigned>::type>::type;
+};
+
+// Loads kC elements at p (vector-aligned) and decodes them, times `inv`.
+template <int kC, typename T>
+__device__ __forceinline__ void load_vec(const T *p, float (&o)[kC], float inv,
+                                         bool global) {
+  using V = typename Vec<kC, T>::type;
+  union {
+    V v;
+    T e[kC];
+  } u;
+  u.v = global ? __ldg(reinterpret_cast<const V *>(p))
+               : *reinterpret_cast<const V *>(p);
+#pragma unroll
+  for (int j = 0; j < kC; ++j) o[j] = Storage<T>::decode(u.e[j]) * inv;
 }
 
-template <int kC>
-__device__ __forceinline__ void store_vec(float *p, const float (&v)[kC]) {
-  if constexpr (kC == 4) {
-    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
-  } else {
-    *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
-  }
+// Encodes kC values times `scale` and stores them as one vector.
+template <int kC, typename T>
+__device__ __forceinline__ void store_vec(T *p, const float (&v)[kC],
+                                          float scale) {
+  using V = typename Vec<kC, T>::type;
+  union {
+    V v;
+    T e[kC];
+  } u;
+#pragma unroll
+  for (int j = 0; j < kC; ++j) u.e[j] = Storage<T>::encode(v[j] * scale);
+  *reinterpret_cast<V *>(p) = u.v;
 }
 
 // One source row as loaded: kC columns of raw fields and their node types.
@@ -125,9 +173,13 @@ __device__ __forceinline__ unsigned byte_bits(unsigned v) {
   }
 }
 
-template <int kC>
+template <int kC, typename T>
 __device__ __forceinline__ void load_row(const StepLaunch &a, int64_t r,
                                          int64_t xb, RawRow<kC> &o) {
+  using S = Storage<T>;
+  const T *sd = static_cast<const T *>(a.src.d);
+  const T *sx = static_cast<const T *>(a.src.jx);
+  const T *sy = static_cast<const T *>(a.src.jy);
 #pragma unroll
   for (int j = 0; j < kC; ++j) o.d[j] = o.jx[j] = o.jy[j] = 0.f;
   o.solid = (1u << kC) - 1u;
@@ -138,9 +190,9 @@ __device__ __forceinline__ void load_row(const StepLaunch &a, int64_t r,
   }
   const int64_t row = r * a.pitch;
   if (xb >= 0 && xb + kC <= a.nx) {
-    load_vec<kC>(a.src.d + row + xb, o.d);
-    load_vec<kC>(a.src.jx + row + xb, o.jx);
-    load_vec<kC>(a.src.jy + row + xb, o.jy);
+    load_vec<kC, T>(sd + row + xb, o.d, 1.0f / S::kD, true);
+    load_vec<kC, T>(sx + row + xb, o.jx, 1.0f / S::kJ, true);
+    load_vec<kC, T>(sy + row + xb, o.jy, 1.0f / S::kJ, true);
     unsigned m;
     if constexpr (kC == 4)
       m = __ldg(reinterpret_cast<const unsigned *>(a.mask + row + xb));
@@ -160,9 +212,9 @@ __device__ __forceinline__ void load_row(const StepLaunch &a, int64_t r,
       in = true;
     }
     if (in) {
-      o.d[j] = __ldg(a.src.d + row + x);
-      o.jx[j] = __ldg(a.src.jx + row + x);
-      o.jy[j] = __ldg(a.src.jy + row + x);
+      o.d[j] = S::decode(sd[row + x]) * (1.0f / S::kD);
+      o.jx[j] = S::decode(sx[row + x]) * (1.0f / S::kJ);
+      o.jy[j] = S::decode(sy[row + x]) * (1.0f / S::kJ);
       const unsigned t = __ldg(a.mask + row + x);
       solid |= (t == 1u) << j;
       fluid |= (t == 0u) << j;
@@ -255,13 +307,15 @@ __device__ __forceinline__ void fence_async_shared() {
 // Geometry of one ring stage for kC columns per lane: the field window starts
 // at column x0 - 4 (16-byte aligned) and covers the warp's kLanes * kC
 // columns; the node-type window starts at the 16-byte boundary at or below it.
-template <int kC>
+template <int kC, typename T>
 struct Stage {
-  static constexpr int kWin = ((kLanes * kC + (4 - kC)) + 3) / 4 * 4;  // floats
-  static constexpr int kFieldBytes = kWin * 4;
-  static constexpr int kMaskBytes = (kWin + 12 + 15) / 16 * 16;
+  static constexpr int kAlignElems = 16 / static_cast<int>(sizeof(T));
+  // window of elements from ws, the kAlignElems boundary at or below x0 - kC
+  static constexpr int kWin =
+      (kAlignElems - 1 + kLanes * kC + kAlignElems - 1) / kAlignElems * kAlignElems;
+  static constexpr int kFieldBytes = kWin * static_cast<int>(sizeof(T));
+  static constexpr int kMaskBytes = (kWin + 15 + 15) / 16 * 16;
   static constexpr int kBytes = 3 * kFieldBytes + kMaskBytes;
-  static constexpr int kLaneOffset = 4 - kC;  // first column of lane 0
 };
 
 // Sums of w_k (1, c_k) over the solid neighbours of a node, indexed by the
@@ -296,20 +350,21 @@ __device__ __forceinline__ void build_solid_lut(SolidSums *lut) {
 // so rows (r-1, r) are complete after pair S:
 //   out(r-1) = North(S).x + Same(S').y + South(S').x,
 //   out(r)   = North(S).y + Same(S).x  + South(S').y.
-template <int kC, int kS>
+template <typename T, int kC, int kS>
 __host__ __device__ constexpr int ring_bytes() {
-  return 128 + kS * Stage<kC>::kBytes;  // barriers, then the stages
+  return 128 + kS * Stage<kC, T>::kBytes;  // barriers, then the stages
 }
 
-template <int kC, int kS>
+template <typename T, int kC, int kS>
 __host__ __device__ constexpr int smem_bytes() {
-  return 512 * static_cast<int>(sizeof(SolidSums)) + kWarps * ring_bytes<kC, kS>();
+  return 512 * static_cast<int>(sizeof(SolidSums)) +
+         kWarps * ring_bytes<T, kC, kS>();
 }
 
 // One block tile (bx, by) of a step: kWarps warp tiles of (30 kC) columns x
 // kRows rows stacked vertically.  `gx` is the number of tiles along x (for the
 // index of the block's reduction partial).  Every thread of the block calls it.
-template <int kC, int kRows, int kS, bool kReduce>
+template <typename T, int kC, int kRows, int kS, bool kReduce>
 __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
                                           int64_t by, int64_t gx,
                                           const SolidSums *lut,
@@ -317,7 +372,8 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
   static_assert(kRows % 2 == 0, "rows per warp must be even");
   static_assert(kS >= 4 && kS % 2 == 0 && kS <= 16, "ring stages");
   constexpr int kTile = (kLanes - 2) * kC;
-  using St = Stage<kC>;
+  using St = Stage<kC, T>;
+  using SS = Storage<T>;
 
   const int lane = threadIdx.x & (kLanes - 1);
   const int warp = threadIdx.x / kLanes;
@@ -326,14 +382,17 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
   const int64_t y0 = (by * kWarps + warp) * kRows;
   const int64_t y1 = min(y0 + kRows, a.ny);
   const bool owner = lane >= 1 && lane <= kLanes - 2 && xb < a.nx;
-  // interior tiles stream rows through the shared-memory ring
-  const bool bulk = x0 - 4 >= 0 && x0 - 4 + St::kWin <= a.nx;
+  // interior tiles stream rows through the shared-memory ring; the window
+  // starts at ws, the 16-byte boundary at or below the first column x0 - kC
+  const int64_t ws = (x0 - kC) & ~int64_t(St::kAlignElems - 1);
+  const bool bulk = x0 - kC >= 0 && ws + St::kWin <= a.nx;
   unsigned char *ring =
-      smem + 512 * sizeof(SolidSums) + warp * ring_bytes<kC, kS>();
+      smem + 512 * sizeof(SolidSums) + warp * ring_bytes<T, kC, kS>();
   uint64_t *bars = reinterpret_cast<uint64_t *>(ring);
   unsigned char *stages = ring + 128;
-  const int64_t m0 = (x0 - 4) & ~int64_t(15);  // node-type window start
-  const int moff = static_cast<int>(x0 - 4 - m0);
+  const int64_t m0 = ws & ~int64_t(15);  // node-type window start
+  const int c_lane = static_cast<int>(x0 - kC - ws) + kC * lane;
+  const int m_lane = static_cast<int>(ws - m0) + c_lane;
   const float fx = a.fx, fy = a.fy;
   const float2 F2x = bc(fx), F2y = bc(fy), F22y = bc(2.0f * fy);
   const float2 one = bc(1.0f), c3 = bc(3.0f), cm15 = bc(-1.5f), c9 = bc(9.0f);
@@ -378,18 +437,20 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
         return;
       }
       unsigned char *dst = stages + st * St::kBytes;
-      const int64_t off = r * a.pitch + (x0 - 4);
+      const int64_t off = r * a.pitch + ws;
       mbar_expect_tx(bar, St::kBytes);
-      bulk_copy(dst, a.src.d + off, St::kFieldBytes, bar);
-      bulk_copy(dst + St::kFieldBytes, a.src.jx + off, St::kFieldBytes, bar);
-      bulk_copy(dst + 2 * St::kFieldBytes, a.src.jy + off, St::kFieldBytes, bar);
+      bulk_copy(dst, static_cast<const T *>(a.src.d) + off, St::kFieldBytes, bar);
+      bulk_copy(dst + St::kFieldBytes, static_cast<const T *>(a.src.jx) + off,
+                St::kFieldBytes, bar);
+      bulk_copy(dst + 2 * St::kFieldBytes,
+                static_cast<const T *>(a.src.jy) + off, St::kFieldBytes, bar);
       bulk_copy(dst + 3 * St::kFieldBytes, a.mask + r * a.pitch + m0,
                 St::kMaskBytes, bar);
     };
     // ring row i -> registers; false when the copy did not arrive in time
     auto fetch = [&](int64_t i, RawRow<kC> &o) -> bool {
       if (!bulk) {
-        load_row<kC>(a, y0 - 1 + i, xb, o);
+        load_row<kC, T>(a, y0 - 1 + i, xb, o);
         return true;
       }
       if (source_row(i) < 0) {
@@ -402,30 +463,20 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
       const int st = static_cast<int>(i % kS);
       const bool ok = mbar_wait(bars + st, static_cast<uint32_t>((i / kS) & 1));
       const unsigned char *src = stages + st * St::kBytes;
-      const int c = St::kLaneOffset + kC * lane;
-      if constexpr (kC == 4) {
-        const float4 d = *reinterpret_cast<const float4 *>(src + 4 * c);
-        const float4 x = *reinterpret_cast<const float4 *>(src + St::kFieldBytes + 4 * c);
-        const float4 y = *reinterpret_cast<const float4 *>(src + 2 * St::kFieldBytes + 4 * c);
-        o.d[0] = d.x; o.d[1] = d.y; o.d[2] = d.z; o.d[3] = d.w;
-        o.jx[0] = x.x; o.jx[1] = x.y; o.jx[2] = x.z; o.jx[3] = x.w;
-        o.jy[0] = y.x; o.jy[1] = y.y; o.jy[2] = y.z; o.jy[3] = y.w;
-        const unsigned m = *reinterpret_cast<const unsigned *>(
-            src + 3 * St::kFieldBytes + moff + c);
-        o.solid = byte_bits<kC>(m);
-        o.fluid = byte_bits<kC>(~(m | (m >> 1)));
-      } else {
-        const float2 d = *reinterpret_cast<const float2 *>(src + 4 * c);
-        const float2 x = *reinterpret_cast<const float2 *>(src + St::kFieldBytes + 4 * c);
-        const float2 y = *reinterpret_cast<const float2 *>(src + 2 * St::kFieldBytes + 4 * c);
-        o.d[0] = d.x; o.d[1] = d.y;
-        o.jx[0] = x.x; o.jx[1] = x.y;
-        o.jy[0] = y.x; o.jy[1] = y.y;
-        const unsigned m = *reinterpret_cast<const unsigned short *>(
-            src + 3 * St::kFieldBytes + moff + c);
-        o.solid = byte_bits<kC>(m);
-        o.fluid = byte_bits<kC>(~(m | (m >> 1)));
-      }
+      const T *fd = reinterpret_cast<const T *>(src);
+      const T *fx_ = reinterpret_cast<const T *>(src + St::kFieldBytes);
+      const T *fy_ = reinterpret_cast<const T *>(src + 2 * St::kFieldBytes);
+      load_vec<kC, T>(fd + c_lane, o.d, 1.0f / SS::kD, false);
+      load_vec<kC, T>(fx_ + c_lane, o.jx, 1.0f / SS::kJ, false);
+      load_vec<kC, T>(fy_ + c_lane, o.jy, 1.0f / SS::kJ, false);
+      const unsigned char *mk = src + 3 * St::kFieldBytes + m_lane;
+      unsigned m;
+      if constexpr (kC == 4)
+        m = *reinterpret_cast<const unsigned *>(mk);
+      else
+        m = *reinterpret_cast<const unsigned short *>(mk);
+      o.solid = byte_bits<kC>(m);
+      o.fluid = byte_bits<kC>(~(m | (m >> 1)));
       return ok;
     };
     int64_t issued = 0;
@@ -604,17 +655,20 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
         south_my[j] = Tmy;
       }
       if (owner) {
+        T *dd = static_cast<T *>(a.dst.d);
+        T *dx = static_cast<T *>(a.dst.jx);
+        T *dy = static_cast<T *>(a.dst.jy);
         if (r - 1 >= y0) {
           const int64_t o = (r - 1) * a.pitch + xb;
-          store_vec<kC>(a.dst.d + o, od0);
-          store_vec<kC>(a.dst.jx + o, ox0);
-          store_vec<kC>(a.dst.jy + o, oy0);
+          store_vec<kC, T>(dd + o, od0, SS::kD);
+          store_vec<kC, T>(dx + o, ox0, SS::kJ);
+          store_vec<kC, T>(dy + o, oy0, SS::kJ);
         }
         if (r >= y0 && r < y1) {
           const int64_t o = r * a.pitch + xb;
-          store_vec<kC>(a.dst.d + o, od1);
-          store_vec<kC>(a.dst.jx + o, ox1);
-          store_vec<kC>(a.dst.jy + o, oy1);
+          store_vec<kC, T>(dd + o, od1, SS::kD);
+          store_vec<kC, T>(dx + o, ox1, SS::kJ);
+          store_vec<kC, T>(dy + o, oy1, SS::kJ);
         }
       }
       // Shift the window by one pair.
@@ -678,22 +732,22 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
   }
 }
 
-template <int kC, int kRows, int kMinBlocks, int kS, bool kReduce>
+template <typename T, int kC, int kRows, int kMinBlocks, int kS, bool kReduce>
 __global__ void __launch_bounds__(kThreads, kMinBlocks)
     lbm_step_kernel(const StepLaunch a) {
   extern __shared__ __align__(128) unsigned char smem[];
   SolidSums *lut = reinterpret_cast<SolidSums *>(smem);
   build_solid_lut(lut);
   __syncthreads();
-  step_tile<kC, kRows, kS, kReduce>(a, blockIdx.x, blockIdx.y, gridDim.x, lut,
-                                    smem);
+  step_tile<T, kC, kRows, kS, kReduce>(a, blockIdx.x, blockIdx.y, gridDim.x,
+                                       lut, smem);
 }
 
 // Batched step: a persistent grid takes block tiles of many domains from one
 // work list through an atomic counter, so that one launch advances every
 // member of a batch by one step.  Tile for tile it runs the same code as the
 // single-domain kernel, so each member's result does not depend on the batch.
-template <int kC, int kRows, int kMinBlocks, int kS, bool kReduce>
+template <typename T, int kC, int kRows, int kMinBlocks, int kS, bool kReduce>
 __global__ void __launch_bounds__(kThreads, kMinBlocks)
     lbm_batch_kernel(const BatchLaunch b) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -724,7 +778,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks)
     a.fy = m.fy;
     a.partials = m.partials;
     a.flag = m.flag;
-    step_tile<kC, kRows, kS, kReduce>(a, w.y, w.z, m.gx, lut, smem);
+    a.storage = b.storage;
+    step_tile<T, kC, kRows, kS, kReduce>(a, w.y, w.z, m.gx, lut, smem);
   }
 }
 
@@ -775,44 +830,56 @@ __global__ void __launch_bounds__(kFinalizeThreads)
   if (threadIdx.x < 3) out[threadIdx.x] = buf[threadIdx.x][0];
 }
 
+template <typename T>
 __global__ void pack_kernel(const double *__restrict__ staging, Fields f,
                             int64_t nx, int64_t pitch, int64_t y0,
                             int64_t rows) {
+  using S = Storage<T>;
   const int64_t n = nx * rows;
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
        i < n; i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const int64_t y = y0 + i / nx, x = i % nx;
     const int64_t o = y * pitch + x;
-    f.d[o] = static_cast<float>(staging[i] - 1.0);
-    f.jx[o] = static_cast<float>(staging[n + i]);
-    f.jy[o] = static_cast<float>(staging[2 * n + i]);
+    static_cast<T *>(f.d)[o] =
+        S::encode(static_cast<float>(staging[i] - 1.0) * S::kD);
+    static_cast<T *>(f.jx)[o] =
+        S::encode(static_cast<float>(staging[n + i]) * S::kJ);
+    static_cast<T *>(f.jy)[o] =
+        S::encode(static_cast<float>(staging[2 * n + i]) * S::kJ);
   }
 }
 
+template <typename T>
 __global__ void unpack_kernel(Fields f, const uint8_t *__restrict__ mask,
                               double *__restrict__ staging, int64_t nx,
                               int64_t pitch, int64_t y0, int64_t rows) {
+  using S = Storage<T>;
   const int64_t n = nx * rows;
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
        i < n; i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const int64_t y = y0 + i / nx, x = i % nx;
     const int64_t o = y * pitch + x;
     const bool solid = mask[o] == 1u;  // holds no fluid state: report rest
-    staging[i] = solid ? 1.0 : 1.0 + static_cast<double>(f.d[o]);
-    staging[n + i] = solid ? 0.0 : static_cast<double>(f.jx[o]);
-    staging[2 * n + i] = solid ? 0.0 : static_cast<double>(f.jy[o]);
+    const float d = S::decode(static_cast<const T *>(f.d)[o]) * (1.0f / S::kD);
+    const float jx = S::decode(static_cast<const T *>(f.jx)[o]) * (1.0f / S::kJ);
+    const float jy = S::decode(static_cast<const T *>(f.jy)[o]) * (1.0f / S::kJ);
+    staging[i] = solid ? 1.0 : 1.0 + static_cast<double>(d);
+    staging[n + i] = solid ? 0.0 : static_cast<double>(jx);
+    staging[2 * n + i] = solid ? 0.0 : static_cast<double>(jy);
   }
 }
 
 // Writes the solid-node storage values rho - 1 = 0, j = -F.
+template <typename T>
 __global__ void solid_storage_kernel(Fields f, const uint8_t *__restrict__ mask,
                                      int64_t n, float fx, float fy) {
+  using S = Storage<T>;
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
        i < n; i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     if (mask[i] == 1u) {
-      f.d[i] = 0.f;
-      f.jx[i] = -fx;
-      f.jy[i] = -fy;
+      static_cast<T *>(f.d)[i] = S::encode(0.0f);
+      static_cast<T *>(f.jx)[i] = S::encode(-fx * S::kJ);
+      static_cast<T *>(f.jy)[i] = S::encode(-fy * S::kJ);
     }
   }
 }
@@ -844,11 +911,13 @@ dim3 step_grid(int64_t nx, int64_t ny) {
   return dim3(static_cast<unsigned>(gx), static_cast<unsigned>(gy), 1);
 }
 
-template <int kV, bool kReduce>
+template <typename T, int kV, bool kReduce>
 cudaError_t launch_variant(const StepLaunch &a, dim3 g, cudaStream_t s) {
   constexpr Variant v = kVariants[kV];
-  constexpr int smem = smem_bytes<v.cols, v.stages>();
-  auto kern = lbm_step_kernel<v.cols, v.rows, v.min_blocks, v.stages, kReduce>;
+  constexpr int smem = smem_bytes<T, v.cols, v.stages>();
+  static_assert(smem <= 227 * 1024, "shared memory per block");
+  auto kern =
+      lbm_step_kernel<T, v.cols, v.rows, v.min_blocks, v.stages, kReduce>;
   static cudaError_t attr = cudaFuncSetAttribute(
       kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (attr != cudaSuccess) return attr;
@@ -857,26 +926,22 @@ cudaError_t launch_variant(const StepLaunch &a, dim3 g, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <bool kReduce>
+template <typename T, bool kReduce>
 cudaError_t launch_any(const StepLaunch &a, dim3 g, cudaStream_t s) {
   switch (active_variant()) {
-    case 1: return launch_variant<1, kReduce>(a, g, s);
-    case 2: return launch_variant<2, kReduce>(a, g, s);
-    case 3: return launch_variant<3, kReduce>(a, g, s);
-    default: return launch_variant<0, kReduce>(a, g, s);
+    case 1: return launch_variant<T, 1, kReduce>(a, g, s);
+    case 2: return launch_variant<T, 2, kReduce>(a, g, s);
+    case 3: return launch_variant<T, 3, kReduce>(a, g, s);
+    default: return launch_variant<T, 0, kReduce>(a, g, s);
   }
 }
 
-int copy_grid(int64_t n) {
-  const int64_t b = (n + 255) / 256;
-  return static_cast<int>(b < 4096 ? (b < 1 ? 1 : b) : 4096);
-}
-
-template <int kV, bool kReduce>
+template <typename T, int kV, bool kReduce>
 cudaError_t launch_batch_variant(const BatchLaunch &b, cudaStream_t s) {
   constexpr Variant v = kVariants[kV];
-  constexpr int smem = smem_bytes<v.cols, v.stages>();
-  auto kern = lbm_batch_kernel<v.cols, v.rows, v.min_blocks, v.stages, kReduce>;
+  constexpr int smem = smem_bytes<T, v.cols, v.stages>();
+  auto kern =
+      lbm_batch_kernel<T, v.cols, v.rows, v.min_blocks, v.stages, kReduce>;
   // persistent grid: every resident block slot of the device, computed once
   static int grid = [&] {
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -897,14 +962,27 @@ cudaError_t launch_batch_variant(const BatchLaunch &b, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <bool kReduce>
+template <typename T, bool kReduce>
 cudaError_t launch_batch_any(int v, const BatchLaunch &b, cudaStream_t s) {
   switch (v) {
-    case 1: return launch_batch_variant<1, kReduce>(b, s);
-    case 2: return launch_batch_variant<2, kReduce>(b, s);
-    case 3: return launch_batch_variant<3, kReduce>(b, s);
-    default: return launch_batch_variant<0, kReduce>(b, s);
+    case 1: return launch_batch_variant<T, 1, kReduce>(b, s);
+    case 2: return launch_batch_variant<T, 2, kReduce>(b, s);
+    case 3: return launch_batch_variant<T, 3, kReduce>(b, s);
+    default: return launch_batch_variant<T, 0, kReduce>(b, s);
   }
+}
+
+template <typename T>
+cudaError_t launch_step_t(const StepLaunch &a, bool reduce, cudaStream_t s) {
+  const dim3 g = step_grid(a.nx, a.ny);
+  return reduce ? launch_any<T, true>(a, g, s) : launch_any<T, false>(a, g, s);
+}
+
+template <typename T>
+cudaError_t launch_batch_t(int v, const BatchLaunch &b, bool reduce,
+                           cudaStream_t s) {
+  return reduce ? launch_batch_any<T, true>(v, b, s)
+                : launch_batch_any<T, false>(v, b, s);
 }
 
 }  // namespace
@@ -935,8 +1013,11 @@ int default_variant() { return active_variant(); }
 cudaError_t launch_batch(int v, const BatchLaunch &b, bool reduce,
                          cudaStream_t s) {
   if (v < 0 || v >= kNumVariants) return cudaErrorInvalidValue;
-  return reduce ? launch_batch_any<true>(v, b, s)
-                : launch_batch_any<false>(v, b, s);
+  switch (b.storage) {
+    case kStorageF16: return launch_batch_t<__half>(v, b, reduce, s);
+    case kStorageBF16: return launch_batch_t<__nv_bfloat16>(v, b, reduce, s);
+    default: return launch_batch_t<float>(v, b, reduce, s);
+  }
 }
 
 cudaError_t launch_batch_finalize(const BatchMember *members, int nmembers,
@@ -962,8 +1043,11 @@ int64_t launched_blocks(int64_t nx, int64_t ny) {
 }
 
 cudaError_t launch_step(const StepLaunch &a, bool reduce, cudaStream_t s) {
-  const dim3 g = step_grid(a.nx, a.ny);
-  return reduce ? launch_any<true>(a, g, s) : launch_any<false>(a, g, s);
+  switch (a.storage) {
+    case kStorageF16: return launch_step_t<__half>(a, reduce, s);
+    case kStorageBF16: return launch_step_t<__nv_bfloat16>(a, reduce, s);
+    default: return launch_step_t<float>(a, reduce, s);
+  }
 }
 
 cudaError_t launch_finalize(const double *partials, int64_t nblocks,
@@ -973,29 +1057,73 @@ cudaError_t launch_finalize(const double *partials, int64_t nblocks,
   return cudaGetLastError();
 }
 
-cudaError_t launch_pack(const double *staging, Fields f, int64_t nx,
-                        int64_t pitch, int64_t y0, int64_t rows,
+namespace {
+int copy_grid(int64_t n) {
+  const int64_t b = (n + 255) / 256;
+  return static_cast<int>(b < 4096 ? (b < 1 ? 1 : b) : 4096);
+}
+
+template <typename T>
+cudaError_t pack_t(const double *staging, Fields f, int64_t nx, int64_t pitch,
+                   int64_t y0, int64_t rows, cudaStream_t s) {
+  (void)cudaGetLastError();
+  pack_kernel<T><<<copy_grid(nx * rows), 256, 0, s>>>(staging, f, nx, pitch,
+                                                      y0, rows);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t unpack_t(Fields f, const uint8_t *mask, double *staging,
+                     int64_t nx, int64_t pitch, int64_t y0, int64_t rows,
+                     cudaStream_t s) {
+  (void)cudaGetLastError();
+  unpack_kernel<T><<<copy_grid(nx * rows), 256, 0, s>>>(f, mask, staging, nx,
+                                                        pitch, y0, rows);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t solid_t(Fields f, const uint8_t *mask, int64_t n, float fx,
+                    float fy, cudaStream_t s) {
+  (void)cudaGetLastError();
+  solid_storage_kernel<T><<<copy_grid(n), 256, 0, s>>>(f, mask, n, fx, fy);
+  return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_pack(int storage, const double *staging, Fields f,
+                        int64_t nx, int64_t pitch, int64_t y0, int64_t rows,
                         cudaStream_t s) {
-  (void)cudaGetLastError();
-  pack_kernel<<<copy_grid(nx * rows), 256, 0, s>>>(staging, f, nx, pitch, y0,
-                                                   rows);
-  return cudaGetLastError();
+  switch (storage) {
+    case kStorageF16: return pack_t<__half>(staging, f, nx, pitch, y0, rows, s);
+    case kStorageBF16:
+      return pack_t<__nv_bfloat16>(staging, f, nx, pitch, y0, rows, s);
+    default: return pack_t<float>(staging, f, nx, pitch, y0, rows, s);
+  }
 }
 
-cudaError_t launch_unpack(Fields f, const uint8_t *mask, double *staging,
-                          int64_t nx, int64_t pitch, int64_t y0, int64_t rows,
-                          cudaStream_t s) {
-  (void)cudaGetLastError();
-  unpack_kernel<<<copy_grid(nx * rows), 256, 0, s>>>(f, mask, staging, nx,
-                                                     pitch, y0, rows);
-  return cudaGetLastError();
+cudaError_t launch_unpack(int storage, Fields f, const uint8_t *mask,
+                          double *staging, int64_t nx, int64_t pitch,
+                          int64_t y0, int64_t rows, cudaStream_t s) {
+  switch (storage) {
+    case kStorageF16:
+      return unpack_t<__half>(f, mask, staging, nx, pitch, y0, rows, s);
+    case kStorageBF16:
+      return unpack_t<__nv_bfloat16>(f, mask, staging, nx, pitch, y0, rows, s);
+    default: return unpack_t<float>(f, mask, staging, nx, pitch, y0, rows, s);
+  }
 }
 
-cudaError_t launch_solid_storage(Fields f, const uint8_t *mask, int64_t n,
-                                 float fx, float fy, cudaStream_t s) {
-  (void)cudaGetLastError();
-  solid_storage_kernel<<<copy_grid(n), 256, 0, s>>>(f, mask, n, fx, fy);
-  return cudaGetLastError();
+cudaError_t launch_solid_storage(int storage, Fields f, const uint8_t *mask,
+                                 int64_t n, float fx, float fy,
+                                 cudaStream_t s) {
+  switch (storage) {
+    case kStorageF16: return solid_t<__half>(f, mask, n, fx, fy, s);
+    case kStorageBF16: return solid_t<__nv_bfloat16>(f, mask, n, fx, fy, s);
+    default: return solid_t<float>(f, mask, n, fx, fy, s);
+  }
+}
+
+int storage_bytes(int storage) {
+  return storage == kStorageF16 || storage == kStorageBF16 ? 2 : 4;
 }
 
 }  // namespace lbmtau1

@@ -6,12 +6,18 @@
 
 namespace lbmtau1 {
 
-// Fields of one ping-pong copy: rho - 1 and the momentum j = rho u, FP32,
-// rows of `pitch` elements (pitch % 32 == 0, rows 128-byte aligned).
+// Storage formats (the LBM_STORAGE_* values of the C ABI).
+constexpr int kStorageF32 = 0;
+constexpr int kStorageF16 = 1;
+constexpr int kStorageBF16 = 2;
+int storage_bytes(int storage);  // bytes per stored element
+
+// Fields of one ping-pong copy: rho - 1 and the momentum j = rho u in the
+// storage format, rows of `pitch` elements (pitch % 32 == 0).
 struct Fields {
-  float *d;
-  float *jx;
-  float *jy;
+  void *d;
+  void *jx;
+  void *jy;
 };
 
 struct StepLaunch {
@@ -23,6 +29,7 @@ struct StepLaunch {
   float fx, fy;
   double *partials;     // 3 doubles per block (reduced steps only)
   unsigned int *flag;   // sticky instability flag (reduced steps only)
+  int storage = kStorageF32;
 };
 
 // One member of a batch (see launch_batch): both field copies, the copy that
@@ -49,6 +56,7 @@ struct BatchLaunch {
   const int *nitems;
   unsigned int *counter;  // zeroed before the launch
   int parity;             // step index within the call, mod 2
+  int storage;            // storage format shared by all members
 };
 
 // Tile variants: their number, the block tile size of variant v, and the
@@ -83,17 +91,18 @@ cudaError_t launch_finalize(const double *partials, int64_t nblocks,
 
 // Host-format conversion: rows [y0, y0 + rows) of the state, staged as three
 // consecutive planes of rows*nx doubles (rho, jx, jy).
-cudaError_t launch_pack(const double *staging, Fields f, int64_t nx,
-                        int64_t pitch, int64_t y0, int64_t rows,
+cudaError_t launch_pack(int storage, const double *staging, Fields f,
+                        int64_t nx, int64_t pitch, int64_t y0, int64_t rows,
                         cudaStream_t s);
-cudaError_t launch_unpack(Fields f, const uint8_t *mask, double *staging,
-                          int64_t nx, int64_t pitch, int64_t y0, int64_t rows,
-                          cudaStream_t s);
+cudaError_t launch_unpack(int storage, Fields f, const uint8_t *mask,
+                          double *staging, int64_t nx, int64_t pitch,
+                          int64_t y0, int64_t rows, cudaStream_t s);
 
 // Storage convention of the step kernel: a solid node holds rho - 1 = 0 and
 // j = -F (what a solid source contributes, with no test of the node type).
 // Writes those values into every solid node of f (n = pitch * ny entries).
-cudaError_t launch_solid_storage(Fields f, const uint8_t *mask, int64_t n,
-                                 float fx, float fy, cudaStream_t s);
+cudaError_t launch_solid_storage(int storage, Fields f, const uint8_t *mask,
+                                 int64_t n, float fx, float fy,
+                                 cudaStream_t s);
 
 }  // namespace lbmtau1
