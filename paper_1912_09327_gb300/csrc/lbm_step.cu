@@ -382,6 +382,10 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
   const int64_t y0 = (by * kWarps + warp) * kRows;
   const int64_t y1 = min(y0 + kRows, a.ny);
   const bool owner = lane >= 1 && lane <= kLanes - 2 && xb < a.nx;
+  // columns of this lane that are outputs inside the domain (reductions)
+  unsigned out_cols = 0u;
+#pragma unroll
+  for (int j = 0; j < kC; ++j) out_cols |= (owner && xb + j < a.nx) << j;
   // interior tiles stream rows through the shared-memory ring; the window
   // starts at ws, the 16-byte boundary at or below the first column x0 - kC
   const int64_t ws = (x0 - kC) & ~int64_t(St::kAlignElems - 1);
@@ -494,6 +498,8 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
     for (int64_t k = 0; k < npairs; ++k) {
       consumed = 2 * k;
       const int64_t r = y0 - 1 + 2 * k;  // S = (r, r+1)
+      const bool row0 = r - 1 >= y0;        // output row r - 1 is in the tile
+      const bool row1 = r >= y0 && r < y1;  // output row r is in the tile
       RawRow<kC> ra, rb;
       bool ok = fetch(2 * k, ra);
       ok = fetch(2 * k + 1, rb) && ok;
@@ -628,9 +634,9 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
         ox1[j] = f1 ? mxn.y : jxO.y;
         oy1[j] = f1 ? myn.y : jyO.y;
         if constexpr (kReduce) {
-          const bool col = owner && xb + j < a.nx;
-          const bool v0 = f0 && col && r - 1 >= y0;
-          const bool v1 = f1 && col && r >= y0 && r < y1;
+          const bool col = (out_cols >> j) & 1u;
+          const bool v0 = f0 && col && row0;
+          const bool v1 = f1 && col && row1;
           // u_new - u_old = ((j_n - j_o) + (j_n d_o - j_o d_n)) / (rho_n rho_o)
           const float2 rn = add(dn, one);
           const float2 irn =
