@@ -100,8 +100,12 @@ def load_peak():
     return FALLBACK_HBM_GBS, "fallback (no MEASURED_PEAKS.json)"
 
 
-def kernel_hash():
-    return hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
+def kernel_hash(path=KERNEL_SRC):
+    """Hash of the kernel source's code (comment-only lines and blank lines
+    left out, so that editing a comment does not invalidate a profile)."""
+    code = [l.rstrip() for l in open(path).read().splitlines()
+            if l.strip() and not l.strip().startswith("//")]
+    return hashlib.sha256("\n".join(code).encode()).hexdigest()[:16]
 
 
 def load_traffic(nodes):

@@ -8,7 +8,7 @@
 //   f_k = w_k rho(O)                                if P is solid.
 // Solid and fixed nodes keep their values.
 //
-// Arithmetic form.  The device stores delta = rho - 1 and j in FP32.  With
+// Arithmetic form.  The device stores delta = rho - 1 and j.  With
 // Pi = j' j'^T / rho (j' = j + F) the equilibrium of a source P seen along c is
 //   f^eq_c = w_c (1 + delta + 3 c.j' + 4.5 c^T Pi c - 1.5 tr Pi),
 // so each source contributes a fixed linear combination of six per-node
@@ -23,22 +23,25 @@
 // source enters with delta_P = delta_O, j'_P = 0 and Pi_P = 0, which is
 // Eq. (feqnoslip) in this form.
 //
-// Kernel structure (HBM-bound stencil; no tensor cores).  A warp owns a tile
-// of 120 columns x 32 rows.  Lane l holds the four columns x0 - 4 + 4l ..
-// x0 - 1 + 4l as one float4 per field, so lanes 1..30 own the 120 outputs and
-// lanes 0 and 31 carry the one-column halos (coalesced 512-byte row segments,
-// 16-byte aligned because rows are padded to 32 nodes).  The warp marches
-// down its tile one source row at a time: each source row is read from HBM
-// once, turned into per-node quantities once (one reciprocal per node), the
-// left/right neighbour columns are exchanged with warp shuffles, and the row's
-// contributions are added to the three output rows it feeds (above, same,
-// below).  The output row above is then complete and is stored as float4.
-// The next source row is prefetched into registers while the current one is
-// processed.  Four warps per block stack vertically so that the shared halo
-// rows hit in L1/L2.  Periodic edges and ragged tails take a per-column path.
-// On the last step of an lbm_step call the same kernel also reduces
-// sum |du|^2, sum |u|^2 and sum delta (warp shuffles, FP64 block partials) and
-// raises a sticky flag on rho <= 0 or non-finite values.
+// Kernel structure (HBM-bound stencil; no tensor cores).  A block stacks four
+// warp tiles of 30 kC columns x kRows rows.  Lane l holds kC adjacent columns
+// (one vector per field), so lanes 1..30 own the outputs and lanes 0 and 31
+// carry the one-column halos.  Each warp marches down its tile two source
+// rows at a time; all per-node arithmetic runs on (row r, row r+1) pairs with
+// the packed FP32 instructions (FADD2 / FMUL2 / FFMA2).  Each source row is
+// read from HBM once, turned into per-node quantities once (one reciprocal per
+// node), its left/right neighbour columns come from warp shuffles, and its
+// contributions are added to the output rows it feeds (above, same, below);
+// two output rows complete per pair and are stored as vectors.  Interior warp
+// tiles stream their row windows through a ring of shared-memory stages
+// filled by bulk asynchronous copies (cp.async.bulk completing on mbarriers,
+// every wait bounded in time), several rows ahead of use; edge tiles (periodic
+// wrap, ragged ends) load directly.  On the last step of an lbm_step call the
+// same kernel reduces sum |du|^2, sum |u|^2 and sum delta (warp shuffles, FP64
+// block partials) and raises a sticky flag on rho <= 0 or non-finite values.
+// The storage type T (FP32, or FP16 / BF16 deviations) only changes loads and
+// stores; the arithmetic is FP32 throughout.  A batched kernel runs the same
+// tile code over a work list of many domains' tiles.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <float.h>
