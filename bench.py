@@ -224,7 +224,8 @@ def run_sweep(binding, stream, sizes, steps=200):
         ws = BYTES_PER_LUP * n * n
         out[str(n)] = {"mlups": round(n * n * steps / (ms * 1e3), 1),
                        "gbs_algorithmic": round(ws / (ms / steps) / 1e6, 1),
-                       "l2_resident": bool(2 * ws < l2)}
+                       "l2_resident": bool(2 * ws < l2),
+                       "variant": d.variant()}
         d.close()
         del d
         torch.cuda.empty_cache()
@@ -491,7 +492,7 @@ def main(argv=None):
                 "mlups": round(n * n / (unreduced_ms * 1e3), 1),
                 "gbs_algorithmic": round(BYTES_PER_LUP * n * n / (unreduced_ms * 1e-3) / 1e9, 1),
                 "note": "lbm_step(ctx, 100) / 100: the step kernel without the residual reduction (it runs on the last step only)"},
-            "step_variant": int(os.environ.get("LBMTAU1_STEP_VARIANT", "0")),
+            "step_variant": dom.variant(),
             "gpu_launches": 2 * args.steps,
             "clocks": clocks,
             "residual_last_step": res}

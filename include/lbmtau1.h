@@ -128,6 +128,20 @@ int lbm_set_moments(lbm_ctx *ctx, const double *rho, const double *jx,
 int lbm_step(lbm_ctx *ctx, int64_t nsteps);
 
 /*
+ * Tile variant (block tile shape, 0 .. lbm_variant_count() - 1) of the
+ * context's step kernel.  All variants give bit-identical states; they differ
+ * in how well their grid fills the device.  By default (variant -1) the first
+ * step picks one from the domain size, the SM count and the kernels'
+ * occupancy (the environment variable LBMTAU1_STEP_VARIANT, when set to a
+ * valid index, overrides that choice).  lbm_set_variant may be called between
+ * steps; lbm_variant returns the variant the next step uses, choosing it if
+ * that has not happened yet (-1 for a null context).
+ * Errors: LBM_E_INVAL (variant < -1 or >= lbm_variant_count()).
+ */
+int lbm_set_variant(lbm_ctx *ctx, int32_t variant);
+int32_t lbm_variant(lbm_ctx *ctx);
+
+/*
  * Copies the current state to caller-owned host arrays of nx*ny doubles:
  * density, and momentum jx, jy (velocity = j / rho).  Fixed nodes return the
  * values they hold, solid nodes rho = 1, j = 0.  Synchronises the stream.
@@ -249,8 +263,10 @@ int32_t lbm_batch_members(const lbm_batch *b);
  * LBM_E_CUDA. */
 int lbm_batch_step(lbm_batch *b, int64_t nsteps);
 
-/* Tile variants (block tile shapes) of the step kernel: their count, and the
- * one a batch uses.  All variants give bit-identical states. */
+/* Tile variants (block tile shapes) of the step kernels: their count, and
+ * the one a batch uses (set by hand or by lbm_batch_autotune; the default is
+ * variant 0 unless LBMTAU1_STEP_VARIANT names another).  All variants give
+ * bit-identical states. */
 int32_t lbm_variant_count(void);
 int lbm_batch_set_variant(lbm_batch *b, int32_t variant);
 int32_t lbm_batch_variant(const lbm_batch *b);

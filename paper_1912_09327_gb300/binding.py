@@ -59,6 +59,10 @@ _lib.lbm_set_moments.argtypes = [_vp, _vp, _vp, _vp]
 _lib.lbm_set_moments.restype = ctypes.c_int
 _lib.lbm_step.argtypes = [_vp, ctypes.c_int64]
 _lib.lbm_step.restype = ctypes.c_int
+_lib.lbm_set_variant.argtypes = [_vp, ctypes.c_int32]
+_lib.lbm_set_variant.restype = ctypes.c_int
+_lib.lbm_variant.argtypes = [_vp]
+_lib.lbm_variant.restype = ctypes.c_int32
 _lib.lbm_moments.argtypes = [_vp, _vp, _vp, _vp]
 _lib.lbm_moments.restype = ctypes.c_int
 _lib.lbm_get_state.argtypes = [_vp, _vp, _vp, _vp]
@@ -171,6 +175,15 @@ def lbm_set_moments(ctx, rho, jx, jy) -> None:
 
 def lbm_step(ctx, nsteps: int) -> None:
     _check(_lib.lbm_step(ctx, int(nsteps)), ctx)
+
+
+def lbm_set_variant(ctx, variant: int) -> None:
+    """Tile variant of the context's step kernel; -1 = automatic."""
+    _check(_lib.lbm_set_variant(ctx, int(variant)), ctx)
+
+
+def lbm_variant(ctx) -> int:
+    return int(_lib.lbm_variant(ctx))
 
 
 def lbm_moments(ctx, rho, jx, jy) -> None:
@@ -385,6 +398,12 @@ class Domain:
 
     def step(self, nsteps=1):
         lbm_step(self.ctx, nsteps)
+
+    def set_variant(self, v):
+        lbm_set_variant(self.ctx, v)
+
+    def variant(self):
+        return lbm_variant(self.ctx)
 
     def moments(self, out=None):
         if out is None:

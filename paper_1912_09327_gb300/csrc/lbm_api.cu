@@ -149,6 +149,7 @@ int lbm_create(const lbm_params *p, void *dev_workspace, size_t workspace_bytes,
   c->staging = reinterpret_cast<double *>(c->base + L.off_staging);
   c->stream = static_cast<cudaStream_t>(cuda_stream);
   c->cur = 0;
+  c->variant = -1;
   c->has_geometry = false;
   c->has_residual = false;
   c->n_fluid = 0;
@@ -301,6 +302,9 @@ int lbm_step(lbm_ctx *c, int64_t nsteps) {
   a.partials = c->partials;
   a.flag = c->flag;
   a.storage = c->p.storage;
+  if (c->variant < 0)
+    c->variant = lbmtau1::choose_variant(c->p.nx, c->p.ny, c->p.storage);
+  a.variant = c->variant;
   for (int64_t s = 0; s < nsteps; ++s) {
     a.src = c->f[c->cur];
     a.dst = c->f[1 - c->cur];
@@ -309,11 +313,26 @@ int lbm_step(lbm_ctx *c, int64_t nsteps) {
     c->cur = 1 - c->cur;
   }
   cudaError_t e = lbmtau1::launch_finalize(
-      c->partials, lbmtau1::launched_blocks(c->p.nx, c->p.ny), c->result,
-      c->stream);
+      c->partials, lbmtau1::launched_blocks(c->p.nx, c->p.ny, c->variant),
+      c->result, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "finalize kernel launch");
   c->has_residual = true;
   return LBM_OK;
+}
+
+int lbm_set_variant(lbm_ctx *c, int32_t variant) {
+  if (!c) return LBM_E_INVAL;
+  if (variant < -1 || variant >= lbmtau1::variant_count())
+    return fail(c, LBM_E_INVAL, "variant %d out of range", int(variant));
+  c->variant = variant;
+  return LBM_OK;
+}
+
+int32_t lbm_variant(lbm_ctx *c) {
+  if (!c) return -1;
+  if (c->variant < 0)
+    c->variant = lbmtau1::choose_variant(c->p.nx, c->p.ny, c->p.storage);
+  return c->variant;
 }
 
 int lbm_moments(lbm_ctx *c, double *rho, double *jx, double *jy) {

@@ -36,6 +36,7 @@ struct lbm_ctx {
   double *staging;
   cudaStream_t stream;
   int cur;              // copy holding the current state
+  int variant;          // tile variant, chosen at the first step (-1 before)
   bool has_geometry;
   bool has_residual;
   int64_t n_fluid;

@@ -57,12 +57,14 @@ extern "C" int lbm_step_noalloc(const float *drho_in, const float *jx_in,
   const void *ptrs[7] = {drho_in, jx_in, jy_in, drho_out, jx_out, jy_out, mask};
   for (const void *p : ptrs)
     if (!aligned16(p)) return LBM_E_INVAL;
-  if (lbmtau1::launched_blocks(nx, ny) > kNoAllocMaxBlocks)
-    return LBM_E_INVAL;  // domain larger than the static scratch serves
 
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
     return LBM_E_CUDA;
+  const int variant = lbmtau1::choose_variant(nx, ny, lbmtau1::kStorageF32);
+  const int64_t blocks = lbmtau1::launched_blocks(nx, ny, variant);
+  if (blocks > kNoAllocMaxBlocks)
+    return LBM_E_INVAL;  // domain larger than the static scratch serves
   // Set-up on the first call on each device: the device address of the
   // scratch array (the host-side name is only a stand-in for it).
   std::call_once(g_setup_once[dev], [dev] {
@@ -95,9 +97,9 @@ extern "C" int lbm_step_noalloc(const float *drho_in, const float *jx_in,
   a.fy = static_cast<float>(fy);
   a.partials = partials;
   a.flag = flag;
+  a.variant = variant;
   if (lbmtau1::launch_step(a, true, s) != cudaSuccess) return LBM_E_CUDA;
-  if (lbmtau1::launch_finalize(partials, lbmtau1::launched_blocks(nx, ny),
-                               dev_sums, s) != cudaSuccess)
+  if (lbmtau1::launch_finalize(partials, blocks, dev_sums, s) != cudaSuccess)
     return LBM_E_CUDA;
   if (cudaMemcpyAsync(dev_flags, flag, sizeof(unsigned),
                       cudaMemcpyDeviceToDevice, s) != cudaSuccess)

@@ -45,6 +45,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <float.h>
+#include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 
@@ -898,21 +899,27 @@ __global__ void solid_storage_kernel(Fields f, const uint8_t *__restrict__ mask,
 struct Variant {
   int cols, rows, min_blocks, stages;
 };
-constexpr Variant kVariants[] = {
-    {4, 64, 2, 8}, {2, 64, 3, 12}, {4, 32, 2, 8}, {2, 64, 4, 12}};
+constexpr Variant kVariants[] = {{4, 64, 2, 8},  {2, 64, 3, 12}, {4, 32, 2, 8},
+                                  {2, 64, 4, 12}, {4, 8, 2, 8},   {2, 8, 3, 12}};
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
-int active_variant() {
+// A variant forced through LBMTAU1_STEP_VARIANT (tuning), or -1.
+int forced_variant() {
   static int v = [] {
     const char *e = getenv("LBMTAU1_STEP_VARIANT");
-    int i = e ? atoi(e) : 0;
-    return (i >= 0 && i < kNumVariants) ? i : 0;
+    int i = e ? atoi(e) : -1;
+    return (i >= 0 && i < kNumVariants) ? i : -1;
   }();
   return v;
 }
 
-dim3 step_grid(int64_t nx, int64_t ny) {
-  const Variant v = kVariants[active_variant()];
+int active_variant() {
+  const int f = forced_variant();
+  return f >= 0 ? f : 0;
+}
+
+dim3 step_grid(int64_t nx, int64_t ny, int vi) {
+  const Variant v = kVariants[(vi >= 0 && vi < kNumVariants) ? vi : 0];
   const int64_t tile_x = (kLanes - 2) * v.cols;
   const int64_t tile_y = static_cast<int64_t>(kWarps) * v.rows;
   const int64_t gx = (nx + tile_x - 1) / tile_x;
@@ -937,12 +944,87 @@ cudaError_t launch_variant(const StepLaunch &a, dim3 g, cudaStream_t s) {
 
 template <typename T, bool kReduce>
 cudaError_t launch_any(const StepLaunch &a, dim3 g, cudaStream_t s) {
-  switch (active_variant()) {
+  switch (a.variant) {
     case 1: return launch_variant<T, 1, kReduce>(a, g, s);
     case 2: return launch_variant<T, 2, kReduce>(a, g, s);
     case 3: return launch_variant<T, 3, kReduce>(a, g, s);
+    case 4: return launch_variant<T, 4, kReduce>(a, g, s);
+    case 5: return launch_variant<T, 5, kReduce>(a, g, s);
     default: return launch_variant<T, 0, kReduce>(a, g, s);
   }
+}
+
+// Resident blocks per SM of a variant's (unreduced) step kernel.
+template <typename T, int kV>
+int occupancy_of() {
+  constexpr Variant v = kVariants[kV];
+  constexpr int smem = smem_bytes<T, v.cols, v.stages>();
+  auto kern = lbm_step_kernel<T, v.cols, v.rows, v.min_blocks, v.stages, false>;
+  static int occ = [&] {
+    int n = 0;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, kThreads,
+                                                      smem) != cudaSuccess)
+      n = 0;
+    return n;
+  }();
+  return occ;
+}
+
+template <typename T>
+int occupancy(int v) {
+  switch (v) {
+    case 1: return occupancy_of<T, 1>();
+    case 2: return occupancy_of<T, 2>();
+    case 3: return occupancy_of<T, 3>();
+    case 4: return occupancy_of<T, 4>();
+    case 5: return occupancy_of<T, 5>();
+    default: return occupancy_of<T, 0>();
+  }
+}
+
+// Picks the variant with the shortest expected step time for an nx x ny
+// domain.  The model, fitted to step times measured on a GB300 over the
+// 256^2 .. 16384^2 cavity sweep: blocks are spread evenly over the SMs, so the
+// busiest SM runs ceil(blocks / SMs) of them; one block marches kRows + 2
+// source rows per warp, each costing its columns per lane (two columns per
+// lane cost 1.215 times as much per column as four: fewer loads in flight per
+// instruction); and an SM that holds two or more blocks at once gets through
+// them 1.3 times as fast as one block alone (the kernel is issue-bound, so a
+// second block adds little and a third nothing measurable).
+template <typename T>
+int choose_variant_t(int64_t nx, int64_t ny) {
+  constexpr double kTwoColumnCost = 1.215;
+  constexpr double kSharedSpeedup = 1.3;
+  static int sms = [] {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) !=
+            cudaSuccess)
+      n = 0;
+    return n;
+  }();
+  if (sms <= 0) return 0;
+  int best = 0;
+  double best_time = 0.0;
+  for (int i = 0; i < kNumVariants; ++i) {
+    const Variant v = kVariants[i];
+    const int occ = occupancy<T>(i);
+    if (occ <= 0) continue;
+    const dim3 g = step_grid(nx, ny, i);
+    const int64_t blocks = static_cast<int64_t>(g.x) * g.y;
+    const int64_t per_sm = (blocks + sms - 1) / sms;
+    const double block_time =
+        (v.rows + 2.0) * v.cols * (v.cols == 2 ? kTwoColumnCost : 1.0);
+    const double rate = (occ >= 2 && per_sm >= 2) ? kSharedSpeedup : 1.0;
+    const double t = static_cast<double>(per_sm) * block_time / rate;
+    if (best_time == 0.0 || t < best_time * (1.0 - 1e-9)) {
+      best_time = t;
+      best = i;
+    }
+  }
+  return best;
 }
 
 template <typename T, int kV, bool kReduce>
@@ -977,13 +1059,15 @@ cudaError_t launch_batch_any(int v, const BatchLaunch &b, cudaStream_t s) {
     case 1: return launch_batch_variant<T, 1, kReduce>(b, s);
     case 2: return launch_batch_variant<T, 2, kReduce>(b, s);
     case 3: return launch_batch_variant<T, 3, kReduce>(b, s);
+    case 4: return launch_batch_variant<T, 4, kReduce>(b, s);
+    case 5: return launch_batch_variant<T, 5, kReduce>(b, s);
     default: return launch_batch_variant<T, 0, kReduce>(b, s);
   }
 }
 
 template <typename T>
 cudaError_t launch_step_t(const StepLaunch &a, bool reduce, cudaStream_t s) {
-  const dim3 g = step_grid(a.nx, a.ny);
+  const dim3 g = step_grid(a.nx, a.ny, a.variant);
   return reduce ? launch_any<T, true>(a, g, s) : launch_any<T, false>(a, g, s);
 }
 
@@ -1046,9 +1130,19 @@ cudaError_t launch_batch_gather(const BatchMember *members, int nmembers,
   return cudaGetLastError();
 }
 
-int64_t launched_blocks(int64_t nx, int64_t ny) {
-  const dim3 g = step_grid(nx, ny);
+int64_t launched_blocks(int64_t nx, int64_t ny, int variant) {
+  const dim3 g = step_grid(nx, ny, variant);
   return static_cast<int64_t>(g.x) * g.y;
+}
+
+int choose_variant(int64_t nx, int64_t ny, int storage) {
+  const int f = forced_variant();
+  if (f >= 0) return f;
+  switch (storage) {
+    case kStorageF16: return choose_variant_t<__half>(nx, ny);
+    case kStorageBF16: return choose_variant_t<__nv_bfloat16>(nx, ny);
+    default: return choose_variant_t<float>(nx, ny);
+  }
 }
 
 cudaError_t launch_step(const StepLaunch &a, bool reduce, cudaStream_t s) {

@@ -30,6 +30,7 @@ struct StepLaunch {
   double *partials;     // 3 doubles per block (reduced steps only)
   unsigned int *flag;   // sticky instability flag (reduced steps only)
   int storage = kStorageF32;
+  int variant = 0;      // tile variant (see choose_variant)
 };
 
 // One member of a batch (see launch_batch): both field copies, the copy that
@@ -79,7 +80,13 @@ cudaError_t launch_batch_gather(const BatchMember *members, int nmembers,
 // Upper bound on the thread blocks (reduction partials) of one step launch,
 // over every tile variant; and the count of the variant in use.
 int64_t step_blocks(int64_t nx, int64_t ny);
-int64_t launched_blocks(int64_t nx, int64_t ny);
+int64_t launched_blocks(int64_t nx, int64_t ny, int variant);
+
+// Tile variant for a single-domain step of nx x ny nodes: the one forced by
+// the LBMTAU1_STEP_VARIANT environment variable, else the one whose grid best
+// fills the device (queries the current device once).  All variants give
+// bit-identical results.
+int choose_variant(int64_t nx, int64_t ny, int storage);
 
 // Enqueues one step; `reduce` also writes block partials of
 // (sum |du|^2, sum |u|^2, sum (rho - 1)) and raises the flag on instability.

@@ -106,6 +106,14 @@ def test_call_order_and_arguments_checked_on_host(b):
         z = np.zeros(200)
         assert lib.lbm_set_moments(ctx, z.ctypes.data, z.ctypes.data,
                                    z.ctypes.data) == b.LBM_E_STATE
+        nv = b.lbm_variant_count()
+        assert nv >= 1
+        assert lib.lbm_set_variant(ctx, nv) == b.LBM_E_INVAL
+        assert lib.lbm_set_variant(ctx, -2) == b.LBM_E_INVAL
+        for v in range(nv):
+            assert lib.lbm_set_variant(ctx, v) == b.LBM_OK
+            assert b.lbm_variant(ctx) == v
+        assert lib.lbm_set_variant(ctx, -1) == b.LBM_OK
     finally:
         b.lbm_destroy(ctx)
     assert b.lbm_last_error(None) == "null context"

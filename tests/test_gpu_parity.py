@@ -84,6 +84,44 @@ def test_random_domains(binding, nx, ny, periodic):
         assert np.abs(a - b).max() <= tol
 
 
+@pytest.mark.parametrize("nx,ny,periodic", [(301, 143, (True, False)),
+                                             (1024, 1024, (False, False)),
+                                             (37, 519, (True, True))])
+def test_tile_variants_bit_identical(binding, nx, ny, periodic):
+    """Every tile variant of the single-domain path gives the same state, bit
+    for bit (each output node is computed by the same arithmetic, whatever
+    tile holds it), and the automatic choice is one of them.  The residual
+    and mass are sums whose grouping depends on the tile: each lane adds its
+    own outputs in FP32 (at most 64 rows x 4 columns, a relative error below
+    256 * 2^-24 = 1.5e-5 for the positive sums), the rest is FP64."""
+    p = wl.random_problem(nx, ny, seed=nx + 7 * ny, amp=0.02,
+                          periodic=periodic, force=(1e-4, -5e-5))
+    nv = binding.lbm_variant_count()
+    states, residuals = [], []
+    for v in list(range(nv)) + [-1]:
+        d = binding.Domain.from_problem(p)
+        d.set_variant(v)
+        chosen = d.variant()
+        assert 0 <= chosen < nv and (v < 0 or chosen == v)
+        d.step(9)
+        states.append(d.get_state())
+        residuals.append(d.residual())
+        d.close()
+    for st, r in zip(states[1:], residuals[1:]):
+        for a, b in zip(st, states[0]):
+            assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
+        assert r[0] == pytest.approx(residuals[0][0], rel=1.5e-5)
+        # mass: a signed sum of |rho - 1| <= 0.05 terms
+        assert abs(r[1] - residuals[0][1]) <= 1.5e-5 * 0.05 * nx * ny
+    o = oracle.run(p.mask, *p.state(), 9, p.periodic, p.force)
+    g = [states[0][0].astype(np.float64) + 1.0,
+         states[0][1].astype(np.float64), states[0][2].astype(np.float64)]
+    solid = p.mask == wl.SOLID
+    for a, b in zip(g, o):
+        a[solid] = b[solid]   # solid nodes are stored as (0, -F), reported at rest
+        assert np.abs(a - b).max() <= tolerance(0.02, 9)
+
+
 def test_single_step_exact_paths(binding):
     """One step on an all-fluid periodic box and on a walled box: every node
     is compared with the oracle."""
