@@ -9,8 +9,12 @@ Workload: the lid-driven cavity of Section 3 (walls on three sides, a fixed
 lid row moving at u = 0.1), FP32 storage, at the largest size of the
 256^2 .. 16384^2 single-domain sweep, 16384^2 nodes (6.7 GB of fields and node
 types, far larger than the 129 MB L2, so no L2 flush is needed between steps).
-Smaller sweep sizes, including the 1024^2 cavity itself, are reported beside
-it; those that fit in L2 are marked as such and say nothing about HBM.
+Beside it: the single-domain bandwidth sweep (fully periodic boxes with a
+small random perturbation, 256^2 .. 16384^2, FP32, FP16 and BF16 storage;
+sizes that fit in L2 are marked as such and say nothing about HBM), the
+1024^2 cavity over its 20000 steps, the storage precision on the Poiseuille
+channel, the batched 512-domain configuration (FP32 and FP16) and the serving
+loop.
 
 Multi-GPU: the step does not shard here (one domain per GPU); ``--gpus N``
 under torchrun runs N independent replicas (weak scaling) and reports the sum
@@ -197,21 +201,39 @@ def time_steps(dom, stream, steps):
     return [a.elapsed_time(b) for a, b in ev]
 
 
-def cavity_domain(binding, n, stream):
-    from paper_1912_09327_gb300 import workloads as wl
-    p = wl.cavity(n, 0.1)
-    d = binding.Domain(n, n, p.periodic, p.force, stream=stream)
+def bytes_per_lup(storage="f32"):
+    """Algorithmic bytes per lattice update: rho - 1, jx, jy read and written
+    in the storage format, plus the 1-byte node type."""
+    return 1 + 6 * {"f32": 4, "f16": 2, "bf16": 2}[storage]
+
+
+def problem_domain(binding, p, stream, storage="f32"):
+    ny, nx = p.mask.shape
+    d = binding.Domain(nx, ny, p.periodic, p.force, stream=stream,
+                       storage=storage)
     d.set_geometry(p.mask)
     d.set_moments(p.rho, p.jx, p.jy)
-    return d, p
+    return d
 
 
-def run_sweep(binding, stream, sizes, steps=200):
+def cavity_domain(binding, n, stream, storage="f32"):
+    from paper_1912_09327_gb300 import workloads as wl
+    p = wl.cavity(n, 0.1)
+    return problem_domain(binding, p, stream, storage), p
+
+
+def run_sweep(binding, stream, sizes, storage="f32", steps=200):
+    """Single-domain bandwidth sweep: fully periodic all-fluid boxes with a
+    small random perturbation (delta rho, u ~ 1e-3 N(0, 1)), n x n for each
+    size, in one storage format; `steps` timed steps after 20 warm-up steps
+    (the time of lbm_step(ctx, steps), one reduction at its end)."""
+    from paper_1912_09327_gb300 import workloads as wl
     out = {}
     import torch
     l2 = torch.cuda.get_device_properties(0).L2_cache_size
+    bpl = bytes_per_lup(storage)
     for n in sizes:
-        d, _ = cavity_domain(binding, n, stream)
+        d = problem_domain(binding, wl.periodic_box_tiled(n), stream, storage)
         d.step(20)
         stream.synchronize()
         s = torch.cuda.Event(enable_timing=True)
@@ -221,7 +243,7 @@ def run_sweep(binding, stream, sizes, steps=200):
         e.record(stream)
         stream.synchronize()
         ms = s.elapsed_time(e)
-        ws = BYTES_PER_LUP * n * n
+        ws = bpl * n * n
         out[str(n)] = {"mlups": round(n * n * steps / (ms * 1e3), 1),
                        "gbs_algorithmic": round(ws / (ms / steps) / 1e6, 1),
                        "l2_resident": bool(2 * ws < l2),
@@ -229,6 +251,70 @@ def run_sweep(binding, stream, sizes, steps=200):
         d.close()
         del d
         torch.cuda.empty_cache()
+    return {"workload": "fully periodic all-fluid n^2 box, random "
+                        "perturbation 1e-3, %s storage, %d timed steps"
+                        % (storage, steps),
+            "bytes_per_lup": bpl, "sizes": out}
+
+
+def run_cavity(binding, stream, n=1024, steps=20000):
+    """The lid-driven cavity configuration itself: n x n, lid u = 0.1, FP32,
+    all its steps in one lbm_step call (the working set fits in L2)."""
+    import torch
+    d, _ = cavity_domain(binding, n, stream)
+    s = torch.cuda.Event(enable_timing=True)
+    e = torch.cuda.Event(enable_timing=True)
+    stream.synchronize()
+    s.record(stream)
+    d.step(steps)
+    e.record(stream)
+    res, mass = d.residual()
+    ms = s.elapsed_time(e)
+    out = {"workload": "lid-driven cavity %dx%d, lid u=0.1, FP32, %d steps "
+                       "(one lbm_step call)" % (n, n, steps),
+           "seconds": round(ms / 1e3, 4),
+           "mlups": round(n * n * steps / (ms * 1e3), 1),
+           "residual_last_step": res, "variant": d.variant()}
+    d.close()
+    return out
+
+
+def run_precision(binding, stream, max_steps=60000, chunk=5000):
+    """Storage precision on the Poiseuille channel 64 x 32 (u_max 0.01): run
+    to steady state (residual <= 1e-12, or max_steps) in each storage format,
+    then the relative velocity error against the exact discrete steady state
+    of the method, U(y) = 3 f y (H - y) - f with rho = 1 (it holds for the
+    wall rule of Eq. feqnoslip, so the FP32 figure is rounding alone), and
+    against the plane-Poiseuille parabola u = 3 f y (H - y) (nu = 1/6), whose
+    gap to the former is the method's own 4 / (3 H^2) discretisation error."""
+    from paper_1912_09327_gb300 import workloads as wl
+    p = wl.channel(64, 32, 0.01)
+    f = p.force[0]
+    H = p.meta["H"]
+    y = np.arange(1, H)
+    parabola = 3.0 * f * y * (H - y)
+    exact = parabola - f
+    out = {"workload": "Poiseuille channel 64x32 (x-periodic, walls at "
+                       "y = 0 and 31), u_max 0.01, run to residual 1e-12"}
+    for storage in ("f32", "f16", "bf16"):
+        d = problem_domain(binding, p, stream, storage)
+        steps, res = 0, float("inf")
+        while steps < max_steps:
+            d.step(chunk)
+            steps += chunk
+            res, _ = d.residual()
+            if res <= 1e-12:
+                break
+        R, U, _ = d.moments()
+        d.close()
+        u = (U / R)[1:H, :]
+        out[storage] = {
+            "steps": steps, "residual": res,
+            "err_vs_exact_steady_state": float(
+                np.abs(u - exact[:, None]).max() / exact.max()),
+            "err_vs_parabola": float(
+                np.abs(u - parabola[:, None]).max() / parabola.max())}
+    out["method_discretisation_error"] = 4.0 / (3.0 * H * H)
     return out
 
 
@@ -263,21 +349,21 @@ def run_e2e(binding, dom, n, steps):
             "api": "lbm_set_state + lbm_step(1) + lbm_get_state + lbm_residual, pinned host"}
 
 
-def run_batched(binding, domains, steps, plain_steps=200):
+def run_batched(binding, domains, steps, plain_steps=200, storage="f32"):
     """Configuration: 512 independent domains (seeded thirds of channels,
     cavities and porous samples, sides log-uniform in [64, 1024]), 2000 steps
-    each, FP32; batched (one launch per step for all domains, autotuned tile
-    variant) against the plain form (one domain after another, lbm_step)."""
+    each, in one storage format; batched (one launch per step for all
+    domains, autotuned tile variant) against the plain form (one domain after
+    another, lbm_step)."""
     import torch
     from paper_1912_09327_gb300 import workloads as wl
     probs = wl.batch_mix(domains, seed=0)
     nodes = sum(p.mask.size for p in probs)
     stream = torch.cuda.Stream()
-    doms = [binding.Domain.from_problem(p, stream=stream) for p in probs]
-    tiles = 0
-    for p in probs:
-        ny, nx = p.mask.shape
-        tiles += ((nx + 59) // 60) * ((ny + 127) // 128)  # bound over variants
+    doms = [binding.Domain.from_problem(p, stream=stream, storage=storage)
+            for p in probs]
+    tiles = sum(binding.lbm_tile_count(p.mask.shape[1], p.mask.shape[0])
+                for p in probs)   # the most over the variants the autotuner tries
     batch = binding.Batch(len(doms), tiles, stream=stream)
     for d in doms:
         batch.add(d)
@@ -296,7 +382,8 @@ def run_batched(binding, domains, steps, plain_steps=200):
     torch.cuda.empty_cache()
     # the plain form, one domain after another, timed over plain_steps of the
     # steps (its time per step does not depend on the step) and scaled
-    doms = [binding.Domain.from_problem(p, stream=stream) for p in probs]
+    doms = [binding.Domain.from_problem(p, stream=stream, storage=storage)
+            for p in probs]
     stream.synchronize()
     e0.record(stream)
     for d in doms:
@@ -308,8 +395,8 @@ def run_batched(binding, domains, steps, plain_steps=200):
         d.close()
     torch.cuda.empty_cache()
     return {"workload": "%d domains (channel/cavity/porous thirds, sides "
-                        "log-uniform 64..1024), %d steps each, FP32"
-                        % (domains, steps),
+                        "log-uniform 64..1024), %d steps each, %s storage"
+                        % (domains, steps, storage),
             "nodes": int(nodes), "variant": chosen,
             "autotune_ms_per_step": [round(t, 4) for t in tuned],
             "batched_s": round(t_batch, 4), "plain_s": round(t_plain, 4),
@@ -503,11 +590,18 @@ def main(argv=None):
     del dom
     torch.cuda.empty_cache()
     if rank == 0 and not args.no_sweep:
-        line["sweep"] = run_sweep(binding, stream,
-                                  [256, 512, 1024, 2048, 4096, 8192, 16384])
+        sizes = [256, 512, 1024, 2048, 4096, 8192, 16384]
+        line["sweep"] = run_sweep(binding, stream, sizes)
+        line["sweep_f16"] = run_sweep(binding, stream, sizes, "f16")
+        line["sweep_bf16"] = run_sweep(binding, stream, sizes, "bf16")
+        line["cavity_1024"] = run_cavity(binding, stream)
+        line["precision"] = run_precision(binding, stream)
     if rank == 0 and not args.no_batched:
         line["batched"] = run_batched(binding, args.batched_domains,
                                       args.batched_steps)
+        line["batched_f16"] = run_batched(binding, args.batched_domains,
+                                          args.batched_steps, plain_steps=100,
+                                          storage="f16")
     if rank == 0 and not args.no_serving:
         line["serving"] = run_serving(args.serving_requests)
     if rank == 0 and not args.no_cpu_baseline:

@@ -269,6 +269,12 @@ int lbm_batch_step(lbm_batch *b, int64_t nsteps);
  * bit-identical states. */
 int32_t lbm_variant_count(void);
 int lbm_batch_set_variant(lbm_batch *b, int32_t variant);
+
+/* Block tiles of an nx x ny domain under tile variant `variant`, or the
+ * largest count over all variants for variant -1 (the bound to size a batch
+ * workspace with when the autotuner may try every variant); -1 for invalid
+ * arguments. */
+int64_t lbm_tile_count(int64_t nx, int64_t ny, int32_t variant);
 int32_t lbm_batch_variant(const lbm_batch *b);
 
 /* Autotuner: times steps_per_variant (even, >= 2) batch steps, plus two

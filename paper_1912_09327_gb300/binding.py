@@ -90,6 +90,8 @@ _lib.lbm_batch_step.argtypes = [_vp, ctypes.c_int64]
 _lib.lbm_batch_step.restype = ctypes.c_int
 _lib.lbm_variant_count.argtypes = []
 _lib.lbm_variant_count.restype = ctypes.c_int32
+_lib.lbm_tile_count.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int32]
+_lib.lbm_tile_count.restype = ctypes.c_int64
 _lib.lbm_batch_set_variant.argtypes = [_vp, ctypes.c_int32]
 _lib.lbm_batch_set_variant.restype = ctypes.c_int
 _lib.lbm_batch_variant.argtypes = [_vp]
@@ -272,6 +274,14 @@ def lbm_batch_step(b, nsteps) -> None:
 
 def lbm_variant_count() -> int:
     return int(_lib.lbm_variant_count())
+
+
+def lbm_tile_count(nx: int, ny: int, variant: int = -1) -> int:
+    """Block tiles of an nx x ny domain (variant -1: the most over all)."""
+    n = int(_lib.lbm_tile_count(int(nx), int(ny), int(variant)))
+    if n < 0:
+        raise LbmError(LBM_E_INVAL, "invalid tile count arguments")
+    return n
 
 
 def lbm_batch_set_variant(b, variant) -> None:

@@ -247,6 +247,15 @@ size_t lbm_batch_workspace_bytes(int32_t capacity, int64_t max_tiles) {
 
 int32_t lbm_variant_count(void) { return lbmtau1::variant_count(); }
 
+int64_t lbm_tile_count(int64_t nx, int64_t ny, int32_t variant) {
+  if (nx < 1 || ny < 1 || variant < -1 || variant >= lbmtau1::variant_count())
+    return -1;
+  if (variant < 0) return lbmtau1::step_blocks(nx, ny);
+  int64_t tx = 0, ty = 0;
+  lbmtau1::variant_tile(variant, &tx, &ty);
+  return ((nx + tx - 1) / tx) * ((ny + ty - 1) / ty);
+}
+
 int lbm_batch_create(int32_t capacity, int64_t max_tiles, void *dev_workspace,
                      size_t workspace_bytes, void *cuda_stream,
                      lbm_batch **out) {

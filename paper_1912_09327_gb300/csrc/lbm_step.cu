@@ -35,8 +35,9 @@
 // two output rows complete per pair and are stored as vectors.  Interior warp
 // tiles stream their row windows through a ring of shared-memory stages
 // filled by bulk asynchronous copies (cp.async.bulk completing on mbarriers,
-// every wait bounded in time), several rows ahead of use; edge tiles (periodic
-// wrap, ragged ends) load directly.  On the last step of an lbm_step call the
+// every wait bounded in time), several rows ahead of use; at the domain's
+// edges the copies are clipped to the row and a periodic axis's wrapped
+// column arrives as one more 16-byte block.  On the last step of an lbm_step call the
 // same kernel reduces sum |du|^2, sum |u|^2 and sum delta (warp shuffles, FP64
 // block partials) and raises a sticky flag on rho <= 0 or non-finite values.
 // The storage type T (FP32, or FP16 / BF16 deviations) only changes loads and
@@ -70,9 +71,14 @@ constexpr float k1_12 = 1.0f / 12.0f;  // 3 * (1/36)
 constexpr float k1_3 = 1.0f / 3.0f;    // 3 * (1/9)
 constexpr float k1_6 = 1.0f / 6.0f;    // 2 * (1/12)
 
+// v mod n in [0, n); one period out (the usual case) costs no division.
 __device__ __forceinline__ int64_t wrap_index(int64_t v, int64_t n) {
-  v %= n;
-  return v < 0 ? v + n : v;
+  v = v < 0 ? v + n : (v >= n ? v - n : v);
+  if (v < 0 || v >= n) {
+    v %= n;
+    if (v < 0) v += n;
+  }
+  return v;
 }
 
 // Packed FP32 arithmetic (sm_100 family FADD2 / FMUL2 / FFMA2): every value
@@ -177,66 +183,13 @@ __device__ __forceinline__ unsigned byte_bits(unsigned v) {
   }
 }
 
-template <int kC, typename T>
-__device__ __forceinline__ void load_row(const StepLaunch &a, int64_t r,
-                                         int64_t xb, RawRow<kC> &o) {
-  using S = Storage<T>;
-  const T *sd = static_cast<const T *>(a.src.d);
-  const T *sx = static_cast<const T *>(a.src.jx);
-  const T *sy = static_cast<const T *>(a.src.jy);
-#pragma unroll
-  for (int j = 0; j < kC; ++j) o.d[j] = o.jx[j] = o.jy[j] = 0.f;
-  o.solid = (1u << kC) - 1u;
-  o.fluid = 0u;
-  if (r < 0 || r >= a.ny) {
-    if (!a.periodic_y) return;  // outside a wall-less edge: solid
-    r = wrap_index(r, a.ny);
-  }
-  const int64_t row = r * a.pitch;
-  if (xb >= 0 && xb + kC <= a.nx) {
-    load_vec<kC, T>(sd + row + xb, o.d, 1.0f / S::kD, true);
-    load_vec<kC, T>(sx + row + xb, o.jx, 1.0f / S::kJ, true);
-    load_vec<kC, T>(sy + row + xb, o.jy, 1.0f / S::kJ, true);
-    unsigned m;
-    if constexpr (kC == 4)
-      m = __ldg(reinterpret_cast<const unsigned *>(a.mask + row + xb));
-    else
-      m = __ldg(reinterpret_cast<const unsigned short *>(a.mask + row + xb));
-    o.solid = byte_bits<kC>(m);               // type 1 has bit 0 set
-    o.fluid = byte_bits<kC>(~(m | (m >> 1)));  // type 0 has bits 0, 1 clear
-    return;
-  }
-  unsigned solid = 0u, fluid = 0u;
-#pragma unroll
-  for (int j = 0; j < kC; ++j) {
-    int64_t x = xb + j;
-    bool in = x >= 0 && x < a.nx;
-    if (!in && a.periodic_x) {
-      x = wrap_index(x, a.nx);
-      in = true;
-    }
-    if (in) {
-      o.d[j] = S::decode(sd[row + x]) * (1.0f / S::kD);
-      o.jx[j] = S::decode(sx[row + x]) * (1.0f / S::kJ);
-      o.jy[j] = S::decode(sy[row + x]) * (1.0f / S::kJ);
-      const unsigned t = __ldg(a.mask + row + x);
-      solid |= (t == 1u) << j;
-      fluid |= (t == 0u) << j;
-    } else {
-      solid |= 1u << j;
-    }
-  }
-  o.solid = solid;
-  o.fluid = fluid;
-}
-
 // ---- Row staging through shared memory with the bulk-copy (TMA) engine ----
-// An interior warp tile streams its source rows through a ring of kS shared-
-// memory stages: lane 0 starts `cp.async.bulk` global->shared copies of the
-// tile's row window (three fields and the node types) several rows ahead,
-// each completing on the stage's mbarrier, so the loads in flight do not
-// occupy registers.  Every wait is bounded in time; on expiry the kernel
-// raises kFlagCopyTimeout, drains its copies (again bounded) and stops.
+// Every warp tile streams its source rows through a ring of kS shared-memory
+// stages: lane 0 starts `cp.async.bulk` global->shared copies of the tile's
+// row window (three fields and the node types) several rows ahead, each
+// completing on the stage's mbarrier, so the loads in flight do not occupy
+// registers.  Every wait is bounded in time; on expiry the kernel raises
+// kFlagCopyTimeout, drains its copies (again bounded) and stops.
 constexpr unsigned kFlagUnstable = 1u;
 constexpr unsigned kFlagCopyTimeout = 2u;
 constexpr unsigned long long kWaitLimitNs = 1000000000ull;  // one second
@@ -309,17 +262,20 @@ __device__ __forceinline__ void fence_async_shared() {
 }
 
 // Geometry of one ring stage for kC columns per lane: the field window starts
-// at column x0 - 4 (16-byte aligned) and covers the warp's kLanes * kC
-// columns; the node-type window starts at the 16-byte boundary at or below it.
+// at ws, the 16-byte boundary at or below the warp's first column x0 - kC,
+// and covers its kLanes * kC columns; the node-type window starts at the
+// 16-byte boundary at or below ws.  A side slot after them holds, on a
+// periodic x axis, the 16-byte blocks (three fields, node types) that start
+// the row: column nx seen from the domain's last column.
 template <int kC, typename T>
 struct Stage {
   static constexpr int kAlignElems = 16 / static_cast<int>(sizeof(T));
-  // window of elements from ws, the kAlignElems boundary at or below x0 - kC
   static constexpr int kWin =
       (kAlignElems - 1 + kLanes * kC + kAlignElems - 1) / kAlignElems * kAlignElems;
   static constexpr int kFieldBytes = kWin * static_cast<int>(sizeof(T));
   static constexpr int kMaskBytes = (kWin + 15 + 15) / 16 * 16;
-  static constexpr int kBytes = 3 * kFieldBytes + kMaskBytes;
+  static constexpr int kSideBytes = 4 * 16;
+  static constexpr int kBytes = 3 * kFieldBytes + kMaskBytes + kSideBytes;
 };
 
 // Sums of w_k (1, c_k) over the solid neighbours of a node, indexed by the
@@ -390,15 +346,32 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
   unsigned out_cols = 0u;
 #pragma unroll
   for (int j = 0; j < kC; ++j) out_cols |= (owner && xb + j < a.nx) << j;
-  // interior tiles stream rows through the shared-memory ring; the window
-  // starts at ws, the 16-byte boundary at or below the first column x0 - kC
+  // Row windows.  Of the field window [ws, ws + kWin) and the node-type
+  // window [m0, m0 + kMaskBytes), the bulk copies fill the part inside the
+  // row, [c0, c1) and [k0, k1), rounded out to 16-byte boundaries (which stay
+  // inside the row's pitch).  Other columns read as solid, except that on a
+  // periodic x axis column -1 is column nx - 1 and column nx is column 0: the
+  // 16-byte blocks holding those land in the window head (the tile at x = 0
+  // starts its window one block left of the domain) and in the side slot.
   const int64_t ws = (x0 - kC) & ~int64_t(St::kAlignElems - 1);
-  const bool bulk = x0 - kC >= 0 && ws + St::kWin <= a.nx;
+  const int64_t m0 = ws & ~int64_t(15);
+  const bool interior = ws >= 0 && ws + St::kMaskBytes <= a.nx;
+  const bool wrap_l = a.periodic_x && ws < 0;
+  const bool wrap_r = a.periodic_x && a.nx < x0 + (kLanes - 1) * kC;
+  // this lane's columns that lie in the domain, and the one (if any) that is
+  // column -1 or nx of a periodic x axis, read from the wrapped blocks
+  unsigned in_cols = 0u;
+#pragma unroll
+  for (int j = 0; j < kC; ++j)
+    in_cols |= (xb + j >= 0 && xb + j < a.nx) << j;
+  int wrap_col = -1;
+  if (wrap_l && xb < 0) wrap_col = kC - 1;            // column -1
+  if (wrap_r && xb <= a.nx && a.nx < xb + kC)          // column nx
+    wrap_col = static_cast<int>(a.nx - xb);
   unsigned char *ring =
       smem + 512 * sizeof(SolidSums) + warp * ring_bytes<T, kC, kS>();
   uint64_t *bars = reinterpret_cast<uint64_t *>(ring);
   unsigned char *stages = ring + 128;
-  const int64_t m0 = ws & ~int64_t(15);  // node-type window start
   const int c_lane = static_cast<int>(x0 - kC - ws) + kC * lane;
   const int m_lane = static_cast<int>(ws - m0) + c_lane;
   const float fx = a.fx, fy = a.fy;
@@ -445,22 +418,53 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
         return;
       }
       unsigned char *dst = stages + st * St::kBytes;
-      const int64_t off = r * a.pitch + ws;
-      mbar_expect_tx(bar, St::kBytes);
-      bulk_copy(dst, static_cast<const T *>(a.src.d) + off, St::kFieldBytes, bar);
-      bulk_copy(dst + St::kFieldBytes, static_cast<const T *>(a.src.jx) + off,
-                St::kFieldBytes, bar);
-      bulk_copy(dst + 2 * St::kFieldBytes,
-                static_cast<const T *>(a.src.jy) + off, St::kFieldBytes, bar);
-      bulk_copy(dst + 3 * St::kFieldBytes, a.mask + r * a.pitch + m0,
-                St::kMaskBytes, bar);
+      unsigned char *dmask = dst + 3 * St::kFieldBytes;
+      if (interior) {  // the whole window lies in the row
+        const int64_t off = r * a.pitch + ws;
+        mbar_expect_tx(bar, 3 * St::kFieldBytes + St::kMaskBytes);
+        bulk_copy(dst, static_cast<const T *>(a.src.d) + off, St::kFieldBytes,
+                  bar);
+        bulk_copy(dst + St::kFieldBytes,
+                  static_cast<const T *>(a.src.jx) + off, St::kFieldBytes, bar);
+        bulk_copy(dst + 2 * St::kFieldBytes,
+                  static_cast<const T *>(a.src.jy) + off, St::kFieldBytes, bar);
+        bulk_copy(dmask, a.mask + r * a.pitch + m0, St::kMaskBytes, bar);
+        return;
+      }
+      constexpr int64_t kA = St::kAlignElems;
+      const int64_t c0 = max(ws, int64_t(0));
+      const int64_t c1 = min(ws + St::kWin, (a.nx + kA - 1) & ~(kA - 1));
+      const int64_t k0 = max(m0, int64_t(0));
+      const int64_t k1 = min(m0 + St::kMaskBytes, (a.nx + 15) & ~int64_t(15));
+      const uint32_t fbytes = static_cast<uint32_t>((c1 - c0) * sizeof(T));
+      const uint32_t mbytes = static_cast<uint32_t>(k1 - k0);
+      mbar_expect_tx(bar, 3 * fbytes + mbytes + (wrap_l ? 64u : 0u) +
+                              (wrap_r ? 64u : 0u));
+      const T *src[3] = {static_cast<const T *>(a.src.d) + r * a.pitch,
+                         static_cast<const T *>(a.src.jx) + r * a.pitch,
+                         static_cast<const T *>(a.src.jy) + r * a.pitch};
+      const uint8_t *mrow = a.mask + r * a.pitch;
+      const int64_t foff = (c0 - ws) * static_cast<int64_t>(sizeof(T));
+#pragma unroll
+      for (int f = 0; f < 3; ++f)
+        bulk_copy(dst + f * St::kFieldBytes + foff, src[f] + c0, fbytes, bar);
+      bulk_copy(dmask + (k0 - m0), mrow + k0, mbytes, bar);
+      if (wrap_l) {  // the blocks holding column nx - 1, into the window head
+        const int64_t lf = (a.nx - 1) & ~(kA - 1), lm = (a.nx - 1) & ~int64_t(15);
+#pragma unroll
+        for (int f = 0; f < 3; ++f)
+          bulk_copy(dst + f * St::kFieldBytes, src[f] + lf, 16u, bar);
+        bulk_copy(dmask, mrow + lm, 16u, bar);
+      }
+      if (wrap_r) {  // the blocks holding column 0, into the side slot
+        unsigned char *side = dmask + St::kMaskBytes;
+#pragma unroll
+        for (int f = 0; f < 3; ++f) bulk_copy(side + 16 * f, src[f], 16u, bar);
+        bulk_copy(side + 48, mrow, 16u, bar);
+      }
     };
     // ring row i -> registers; false when the copy did not arrive in time
     auto fetch = [&](int64_t i, RawRow<kC> &o) -> bool {
-      if (!bulk) {
-        load_row<kC, T>(a, y0 - 1 + i, xb, o);
-        return true;
-      }
       if (source_row(i) < 0) {
 #pragma unroll
         for (int j = 0; j < kC; ++j) o.d[j] = o.jx[j] = o.jy[j] = 0.f;
@@ -474,29 +478,53 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
       const T *fd = reinterpret_cast<const T *>(src);
       const T *fx_ = reinterpret_cast<const T *>(src + St::kFieldBytes);
       const T *fy_ = reinterpret_cast<const T *>(src + 2 * St::kFieldBytes);
+      const unsigned char *mw = src + 3 * St::kFieldBytes;
       load_vec<kC, T>(fd + c_lane, o.d, 1.0f / SS::kD, false);
       load_vec<kC, T>(fx_ + c_lane, o.jx, 1.0f / SS::kJ, false);
       load_vec<kC, T>(fy_ + c_lane, o.jy, 1.0f / SS::kJ, false);
-      const unsigned char *mk = src + 3 * St::kFieldBytes + m_lane;
+      const unsigned char *mk = mw + m_lane;
       unsigned m;
       if constexpr (kC == 4)
         m = *reinterpret_cast<const unsigned *>(mk);
       else
         m = *reinterpret_cast<const unsigned short *>(mk);
-      o.solid = byte_bits<kC>(m);
-      o.fluid = byte_bits<kC>(~(m | (m >> 1)));
+      // columns outside the domain are solid (whatever the window holds)
+      o.solid = byte_bits<kC>(m) | (~in_cols & ((1u << kC) - 1u));
+      o.fluid = byte_bits<kC>(~(m | (m >> 1))) & in_cols;
+      if (wrap_col >= 0) {  // column -1 or nx of a periodic x axis
+        const bool left = wrap_col == kC - 1 && xb < 0;
+        // column nx - 1 in the window head, or column 0 in the side slot
+        const int fo = static_cast<int>((a.nx - 1) & (St::kAlignElems - 1));
+        const T *side = reinterpret_cast<const T *>(mw + St::kMaskBytes);
+        const float d = SS::decode(left ? fd[fo] : side[0]) * (1.0f / SS::kD);
+        const float jx = SS::decode(left ? fx_[fo] : side[St::kAlignElems]) *
+                         (1.0f / SS::kJ);
+        const float jy = SS::decode(left ? fy_[fo] : side[2 * St::kAlignElems]) *
+                         (1.0f / SS::kJ);
+        const unsigned t =
+            left ? mw[(a.nx - 1) & 15] : mw[St::kMaskBytes + 48];
+#pragma unroll
+        for (int j = 0; j < kC; ++j) {
+          if (j == wrap_col) {
+            o.d[j] = d;
+            o.jx[j] = jx;
+            o.jy[j] = jy;
+          }
+        }
+        const unsigned bit = 1u << wrap_col;
+        o.solid = (o.solid & ~bit) | ((t == 1u) ? bit : 0u);
+        o.fluid = (o.fluid & ~bit) | ((t == 0u) ? bit : 0u);
+      }
       return ok;
     };
     int64_t issued = 0;
-    if (bulk) {
-      if (lane == 0) {
-        for (int st = 0; st < kS; ++st) mbar_init(bars + st);
-        fence_async_shared();
-        for (; issued < nrows && issued < kS; ++issued) issue(issued);
-      }
-      issued = __shfl_sync(kFull, issued, 0);
-      __syncwarp();
+    if (lane == 0) {
+      for (int st = 0; st < kS; ++st) mbar_init(bars + st);
+      fence_async_shared();
+      for (; issued < nrows && issued < kS; ++issued) issue(issued);
     }
+    issued = __shfl_sync(kFull, issued, 0);
+    __syncwarp();
     bool aborted = false;
     int64_t consumed = 0;
     for (int64_t k = 0; k < npairs; ++k) {
@@ -511,14 +539,12 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
         aborted = true;
         break;
       }
-      if (bulk) {
-        __syncwarp();  // every lane has read both stages
-        if (lane == 0) {
-          fence_async_shared();
-          for (int t = 0; t < 2 && issued < nrows; ++t, ++issued) issue(issued);
-        }
-        issued = __shfl_sync(kFull, issued, 0);
+      __syncwarp();  // every lane has read both stages
+      if (lane == 0) {
+        fence_async_shared();
+        for (int t = 0; t < 2 && issued < nrows; ++t, ++issued) issue(issued);
       }
+      issued = __shfl_sync(kFull, issued, 0);
 
       // Per-node quantities of S, own columns at index j + 1.
       float2 df[kC + 2], zx[kC + 2], zy[kC + 2], A[kC + 2], G[kC + 2],
@@ -703,12 +729,11 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
         mbar_wait(bars + i % kS, static_cast<uint32_t>((i / kS) & 1));
       }
     }
-    if (bulk) {  // release the barriers so the ring can serve another tile
-      __syncwarp();
-      if (lane == 0)
-        for (int st = 0; st < kS; ++st) mbar_inval(bars + st);
-      __syncwarp();
-    }
+    // release the barriers so the ring can serve another tile
+    __syncwarp();
+    if (lane == 0)
+      for (int st = 0; st < kS; ++st) mbar_inval(bars + st);
+    __syncwarp();
   }
 
   if constexpr (kReduce) {
@@ -900,8 +925,21 @@ struct Variant {
   int cols, rows, min_blocks, stages;
 };
 constexpr Variant kVariants[] = {{4, 64, 2, 8},  {2, 64, 3, 12}, {4, 32, 2, 8},
-                                  {2, 64, 4, 12}, {4, 8, 2, 8},   {2, 8, 3, 12}};
+                                  {2, 64, 4, 10}, {4, 8, 2, 8},   {2, 8, 3, 12}};
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
+
+// Calls f(std::integral_constant<int, v>) for a run-time variant index v
+// (variant 0 for an index out of range).
+template <int kV = 0, typename F>
+auto with_variant(int v, F &&f) {
+  if constexpr (kV + 1 < kNumVariants) {
+    if (v == kV) return f(std::integral_constant<int, kV>{});
+    return with_variant<kV + 1>(v, static_cast<F &&>(f));
+  } else {
+    if (v == kV) return f(std::integral_constant<int, kV>{});
+    return f(std::integral_constant<int, 0>{});
+  }
+}
 
 // A variant forced through LBMTAU1_STEP_VARIANT (tuning), or -1.
 int forced_variant() {
@@ -944,14 +982,9 @@ cudaError_t launch_variant(const StepLaunch &a, dim3 g, cudaStream_t s) {
 
 template <typename T, bool kReduce>
 cudaError_t launch_any(const StepLaunch &a, dim3 g, cudaStream_t s) {
-  switch (a.variant) {
-    case 1: return launch_variant<T, 1, kReduce>(a, g, s);
-    case 2: return launch_variant<T, 2, kReduce>(a, g, s);
-    case 3: return launch_variant<T, 3, kReduce>(a, g, s);
-    case 4: return launch_variant<T, 4, kReduce>(a, g, s);
-    case 5: return launch_variant<T, 5, kReduce>(a, g, s);
-    default: return launch_variant<T, 0, kReduce>(a, g, s);
-  }
+  return with_variant(a.variant, [&](auto kv) {
+    return launch_variant<T, decltype(kv)::value, kReduce>(a, g, s);
+  });
 }
 
 // Resident blocks per SM of a variant's (unreduced) step kernel.
@@ -974,14 +1007,9 @@ int occupancy_of() {
 
 template <typename T>
 int occupancy(int v) {
-  switch (v) {
-    case 1: return occupancy_of<T, 1>();
-    case 2: return occupancy_of<T, 2>();
-    case 3: return occupancy_of<T, 3>();
-    case 4: return occupancy_of<T, 4>();
-    case 5: return occupancy_of<T, 5>();
-    default: return occupancy_of<T, 0>();
-  }
+  return with_variant(v, [](auto kv) {
+    return occupancy_of<T, decltype(kv)::value>();
+  });
 }
 
 // Picks the variant with the shortest expected step time for an nx x ny
@@ -1055,14 +1083,9 @@ cudaError_t launch_batch_variant(const BatchLaunch &b, cudaStream_t s) {
 
 template <typename T, bool kReduce>
 cudaError_t launch_batch_any(int v, const BatchLaunch &b, cudaStream_t s) {
-  switch (v) {
-    case 1: return launch_batch_variant<T, 1, kReduce>(b, s);
-    case 2: return launch_batch_variant<T, 2, kReduce>(b, s);
-    case 3: return launch_batch_variant<T, 3, kReduce>(b, s);
-    case 4: return launch_batch_variant<T, 4, kReduce>(b, s);
-    case 5: return launch_batch_variant<T, 5, kReduce>(b, s);
-    default: return launch_batch_variant<T, 0, kReduce>(b, s);
-  }
+  return with_variant(v, [&](auto kv) {
+    return launch_batch_variant<T, decltype(kv)::value, kReduce>(b, s);
+  });
 }
 
 template <typename T>

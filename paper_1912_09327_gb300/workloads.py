@@ -120,6 +120,20 @@ def periodic_box(nx: int, ny: int, seed: int = 0, amp: float = 1e-3) -> Problem:
     return Problem("periodic", mask, (True, True), (0.0, 0.0), r, u, v)
 
 
+def periodic_box_tiled(n: int, seed: int = 0, amp: float = 1e-3,
+                       tile: int = 512) -> Problem:
+    """The bandwidth-sweep domain: a fully periodic, all-fluid n x n box whose
+    small random perturbation (as periodic_box) is drawn on one tile x tile
+    block and repeated, so that large sweep sizes are generated in seconds
+    (the field stays periodic when n is a multiple of the tile)."""
+    t = min(tile, n)
+    r0, u0, v0 = random_state((t, t), seed, amp)
+    reps = (-(-n // t), -(-n // t))
+    r, u, v = (np.tile(a, reps)[:n, :n] for a in (r0, u0, v0))
+    mask = np.zeros((n, n), np.uint8)
+    return Problem("periodic", mask, (True, True), (0.0, 0.0), r, u, v)
+
+
 def random_state(shape, seed: int = 0, amp: float = 1e-3):
     """(rho, rho*u_x, rho*u_y) with rho = 1 + amp N(0,1), u = amp N(0,1)."""
     rng = np.random.default_rng(seed)

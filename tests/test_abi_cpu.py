@@ -114,6 +114,13 @@ def test_call_order_and_arguments_checked_on_host(b):
             assert lib.lbm_set_variant(ctx, v) == b.LBM_OK
             assert b.lbm_variant(ctx) == v
         assert lib.lbm_set_variant(ctx, -1) == b.LBM_OK
+        # tile counts: each variant's grid, and the bound over all of them
+        counts = [b.lbm_tile_count(1000, 700, v) for v in range(nv)]
+        assert all(c >= 1 for c in counts)
+        assert b.lbm_tile_count(1000, 700) == max(counts)
+        assert b.lbm_tile_count(120, 256, 0) == 1      # one 120 x 256 tile
+        assert lib.lbm_tile_count(0, 5, 0) == -1
+        assert lib.lbm_tile_count(5, 5, nv) == -1
     finally:
         b.lbm_destroy(ctx)
     assert b.lbm_last_error(None) == "null context"

@@ -122,6 +122,42 @@ def test_tile_variants_bit_identical(binding, nx, ny, periodic):
         assert np.abs(a - b).max() <= tolerance(0.02, 9)
 
 
+NARROW = [1, 2, 3, 5, 7, 9, 15, 16, 17, 31, 33, 59, 61, 63, 65, 119, 121,
+          123, 125, 127, 129, 241]
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_domain_edges_every_variant(binding, storage):
+    """Widths around every tile and 16-byte boundary, periodic and walled in
+    x: the clipped row windows and the wrapped columns -1 and nx give every
+    tile variant the same state bit for bit, and (FP32) the oracle's."""
+    nv = binding.lbm_variant_count()
+    for i, nx in enumerate(NARROW):
+        per = (i % 2 == 0, i % 3 == 0)
+        p = wl.random_problem(nx, 23, seed=100 + nx, amp=0.02, periodic=per,
+                              force=(1e-4, -5e-5))
+        states = []
+        for v in range(nv):
+            d = binding.Domain(nx, 23, p.periodic, p.force, storage=storage)
+            d.set_geometry(p.mask)
+            d.set_moments(p.rho, p.jx, p.jy)
+            d.set_variant(v)
+            d.step(6)
+            states.append(d.get_state())
+            if v == 0 and storage == "f32":
+                g = d.moments()
+                o = oracle.run(p.mask, *p.state(), 6, p.periodic, p.force)
+                for a, b in zip(g, o):
+                    assert np.abs(a - b).max() <= tolerance(0.02, 6), (nx, per)
+            d.close()
+        for st in states[1:]:
+            for a, b in zip(st, states[0]):
+                assert np.array_equal(a.view(np.uint16 if a.itemsize == 2
+                                             else np.uint32),
+                                      b.view(np.uint16 if b.itemsize == 2
+                                             else np.uint32)), (nx, per)
+
+
 def test_single_step_exact_paths(binding):
     """One step on an all-fluid periodic box and on a walled box: every node
     is compared with the oracle."""
