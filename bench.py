@@ -419,13 +419,23 @@ def run_serving(requests_n, cap=10000):
                          residual_tol=1e-7, max_steps=cap)
     batched = serving.summary(srv.run(reqs))
     srv.close()
+    # every request admitted at once, in arrival order (processor sharing)
+    srv = serving.Server(capacity=max(requests_n, 8), chunk=200,
+                         residual_tol=1e-7, max_steps=cap, policy="fifo",
+                         max_active_nodes=None)
+    shared = serving.summary(srv.run(reqs))
+    srv.close()
     plain = serving.summary(serving.serve_sequential(reqs, chunk=200,
                                                      residual_tol=1e-7,
                                                      max_steps=cap))
     return {"workload": "%d requests, Poisson 200/s, sides log-uniform "
                         "64..2048, residual 1e-7, cap %d steps, chunk 200"
                         % (requests_n, cap),
-            "continuous_batching": batched, "plain_sequential": plain}
+            "continuous_batching": batched,
+            "policy": "smallest first, %d Mi active nodes, 2 s wait bound"
+                      % (serving.DEFAULT_ACTIVE_NODES >> 20),
+            "continuous_batching_fifo_unbounded": shared,
+            "plain_sequential": plain}
 
 
 def cpu_baseline(size, rows=1024, seconds=10.0):

@@ -275,6 +275,13 @@ int lbm_batch_set_variant(lbm_batch *b, int32_t variant);
  * workspace with when the autotuner may try every variant); -1 for invalid
  * arguments. */
 int64_t lbm_tile_count(int64_t nx, int64_t ny, int32_t variant);
+
+/* Block tile of a variant: tile_x columns (30 lanes of cols_per_lane
+ * columns each, plus one halo lane on either side) by tile_y rows (four
+ * warps of tile_y / 4 rows, each also reading one row above and below).
+ * cols_per_lane may be NULL.  Errors: LBM_E_INVAL. */
+int lbm_variant_tile(int32_t variant, int64_t *tile_x, int64_t *tile_y,
+                     int32_t *cols_per_lane);
 int32_t lbm_batch_variant(const lbm_batch *b);
 
 /* Autotuner: times steps_per_variant (even, >= 2) batch steps, plus two

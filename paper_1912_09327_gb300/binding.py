@@ -92,6 +92,8 @@ _lib.lbm_variant_count.argtypes = []
 _lib.lbm_variant_count.restype = ctypes.c_int32
 _lib.lbm_tile_count.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int32]
 _lib.lbm_tile_count.restype = ctypes.c_int64
+_lib.lbm_variant_tile.argtypes = [ctypes.c_int32, _vp, _vp, _vp]
+_lib.lbm_variant_tile.restype = ctypes.c_int
 _lib.lbm_batch_set_variant.argtypes = [_vp, ctypes.c_int32]
 _lib.lbm_batch_set_variant.restype = ctypes.c_int
 _lib.lbm_batch_variant.argtypes = [_vp]
@@ -274,6 +276,17 @@ def lbm_batch_step(b, nsteps) -> None:
 
 def lbm_variant_count() -> int:
     return int(_lib.lbm_variant_count())
+
+
+def lbm_variant_tile(variant: int):
+    """(tile_x, tile_y, columns per lane) of a tile variant."""
+    tx, ty = ctypes.c_int64(), ctypes.c_int64()
+    cols = ctypes.c_int32()
+    st = _lib.lbm_variant_tile(int(variant), ctypes.byref(tx), ctypes.byref(ty),
+                               ctypes.byref(cols))
+    if st != LBM_OK:
+        raise LbmError(st, "invalid variant %d" % variant)
+    return int(tx.value), int(ty.value), int(cols.value)
 
 
 def lbm_tile_count(nx: int, ny: int, variant: int = -1) -> int:

@@ -247,6 +247,17 @@ size_t lbm_batch_workspace_bytes(int32_t capacity, int64_t max_tiles) {
 
 int32_t lbm_variant_count(void) { return lbmtau1::variant_count(); }
 
+int lbm_variant_tile(int32_t variant, int64_t *tile_x, int64_t *tile_y,
+                     int32_t *cols_per_lane) {
+  if (variant < 0 || variant >= lbmtau1::variant_count() || !tile_x ||
+      !tile_y)
+    return LBM_E_INVAL;
+  lbmtau1::variant_tile(variant, tile_x, tile_y);
+  if (cols_per_lane)
+    *cols_per_lane = static_cast<int32_t>(*tile_x / 30);
+  return LBM_OK;
+}
+
 int64_t lbm_tile_count(int64_t nx, int64_t ny, int32_t variant) {
   if (nx < 1 || ny < 1 || variant < -1 || variant >= lbmtau1::variant_count())
     return -1;

@@ -6,9 +6,13 @@ all of them together with the batched step (one launch per time step for the
 whole batch, lbm_batch_step).  Between chunks of steps it reads every member's
 residual with one copy, retires the converged members (their final state is
 downloaded and their memory freed), and admits waiting requests while batch
-slots and the device-memory budget allow: new work joins while older work is
-still on the device.  All arithmetic runs in the library's kernels; this
-module only schedules.
+slots, the device-memory budget and the active-node budget allow: new work
+joins while older work is still on the device.  Waiting requests are taken
+smallest first (fewest nodes), so short solves are not held behind long ones,
+with a bound on how long any request waits before it goes first; the
+active-node budget keeps the batch large enough to fill the GPU but not so
+large that every member's steps slow down.  All arithmetic runs in the
+library's kernels; this module only schedules.
 
 The plain sequential form, `serve_sequential`, solves the same requests one at
 a time in arrival order, for comparison.
@@ -46,6 +50,45 @@ def _footprint(req) -> int:
     return binding.lbm_workspace_bytes(p)
 
 
+def select_next(waiting, now, policy="sjf", max_wait=2.0):
+    """The request to admit next: the one that arrived first under "fifo", or
+    when it has waited longer than `max_wait` seconds; otherwise the one with
+    the fewest nodes (earliest arrival among equals)."""
+    if not waiting:
+        return None
+    oldest = min(waiting, key=lambda r: (r.arrival, r.rid))
+    if policy == "fifo" or now - oldest.arrival > max_wait:
+        return oldest
+    return min(waiting, key=lambda r: (r.nx * r.ny, r.arrival, r.rid))
+
+
+TWO_COLUMN_COST = 1.215  # per column, two columns per lane against four
+
+# Active-node budget of the service: 8 Mi nodes keep a GB300's 152 SMs busy
+# with several waves of block tiles; measured on the 32-request Poisson mix
+# (sides 64..2048) it cuts the median latency by about a quarter against no
+# budget, for a few per cent of throughput and p99.
+DEFAULT_ACTIVE_NODES = 8 << 20
+
+
+def choose_batch_variant(shapes):
+    """Tile variant for a batch of (nx, ny) domains: the one with the least
+    padded work, summed over the members' block tiles.  A tile's work is its
+    marched rows (tile_y plus a halo row above and below each of its four
+    warps) times its 32 lanes' columns, two columns per lane costing
+    TWO_COLUMN_COST times four per column; the persistent batch kernel takes
+    tiles from one work list, so the waves even out."""
+    best, best_cost = 0, None
+    for v in range(binding.lbm_variant_count()):
+        tx, ty, cols = binding.lbm_variant_tile(v)
+        tiles = sum(binding.lbm_tile_count(nx, ny, v) for nx, ny in shapes)
+        cost = tiles * (ty + 8) * 32 * cols * (TWO_COLUMN_COST if cols == 2
+                                               else 1.0)
+        if best_cost is None or cost < best_cost:
+            best, best_cost = v, cost
+    return best
+
+
 def _start(req, stream):
     prob = req.problem()
     dom = binding.Domain.from_problem(prob, stream=stream)
@@ -55,7 +98,8 @@ def _start(req, stream):
 class Server:
     def __init__(self, capacity=256, max_tiles=1 << 20, chunk=200,
                  residual_tol=1e-7, max_steps=20000, hbm_budget=None,
-                 keep_states=False):
+                 keep_states=False, policy="sjf",
+                 max_active_nodes=DEFAULT_ACTIVE_NODES, max_wait=2.0):
         import torch
         self.torch = torch
         self.stream = torch.cuda.Stream()
@@ -67,33 +111,49 @@ class Server:
         free, _ = torch.cuda.mem_get_info()
         self.budget = int(hbm_budget) if hbm_budget else int(0.8 * free)
         self.keep_states = keep_states
+        self.policy = policy
+        self.max_nodes = int(max_active_nodes) if max_active_nodes else None
+        self.max_wait = float(max_wait)
+        self.auto_variant = True
 
     def run(self, requests, clock=time.perf_counter):
         """Serves `requests` (with arrival times in seconds from now);
         returns one Result per request, in request order."""
         pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
-        waiting = collections.deque()
+        waiting = []
         active = {}  # slot -> [req, dom, steps, admitted, bytes]
         used = 0
+        nodes = 0
         done = {}
         t0 = clock()
+        changed = False
         while pending or waiting or active:
             now = clock() - t0
             while pending and pending[0].arrival <= now:
                 waiting.append(pending.popleft())
             while waiting and len(active) < self.capacity:
-                need = _footprint(waiting[0])
-                if used + need > self.budget and active:
-                    break  # wait for memory to free up
-                req = waiting.popleft()
+                req = select_next(waiting, now, self.policy, self.max_wait)
+                need = _footprint(req)
+                size = req.nx * req.ny
+                if active and (used + need > self.budget or
+                               (self.max_nodes is not None and
+                                nodes + size > self.max_nodes)):
+                    break  # wait for memory or node budget to free up
+                waiting.remove(req)
                 dom, _ = _start(req, self.stream)
                 slot = self.batch.add(dom)
                 active[slot] = [req, dom, 0, clock() - t0, need]
                 used += need
+                nodes += size
+                changed = True
             if not active:
                 if pending:
                     time.sleep(max(0.0, pending[0].arrival - (clock() - t0)))
                 continue
+            if changed and self.auto_variant:
+                self.batch.set_variant(choose_batch_variant(
+                    [(e[0].nx, e[0].ny) for e in active.values()]))
+            changed = False
             self.batch.step(self.chunk)
             res, _, status = self.batch.residuals()
             for slot in list(active):
@@ -115,7 +175,9 @@ class Server:
                     self.batch.remove(slot)
                     dom.close()
                     used -= entry[4]
+                    nodes -= req.nx * req.ny
                     del active[slot]
+                    changed = True
         return [done[r.rid] for r in requests]
 
     def close(self):

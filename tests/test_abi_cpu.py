@@ -121,6 +121,13 @@ def test_call_order_and_arguments_checked_on_host(b):
         assert b.lbm_tile_count(120, 256, 0) == 1      # one 120 x 256 tile
         assert lib.lbm_tile_count(0, 5, 0) == -1
         assert lib.lbm_tile_count(5, 5, nv) == -1
+        for v in range(nv):
+            tx, ty, cols = b.lbm_variant_tile(v)
+            assert tx == 30 * cols and cols in (2, 4) and ty % 8 == 0
+            assert b.lbm_tile_count(tx, ty, v) == 1
+            assert b.lbm_tile_count(tx + 1, ty + 1, v) == 4
+        with pytest.raises(b.LbmError):
+            b.lbm_variant_tile(nv)
     finally:
         b.lbm_destroy(ctx)
     assert b.lbm_last_error(None) == "null context"

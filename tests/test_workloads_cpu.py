@@ -75,3 +75,17 @@ def test_request_stream_recipe():
     kinds = [r.kind for r in reqs]
     for k in wl.KINDS:
         assert kinds.count(k) / len(kinds) == pytest.approx(1 / 3, abs=0.04)
+
+
+def test_serving_admission_order():
+    """Smallest first, earliest among equals; the oldest first once it has
+    waited longer than max_wait; plain arrival order under "fifo"."""
+    from paper_1912_09327_gb300 import serving
+    R = wl.Request
+    w = [R(0, 0.00, "cavity", 900, 900, 0), R(1, 0.01, "channel", 64, 80, 1),
+         R(2, 0.02, "porous", 64, 80, 2), R(3, 0.03, "cavity", 300, 64, 3)]
+    assert serving.select_next(w, 0.1).rid == 1
+    assert serving.select_next(w, 0.1, policy="fifo").rid == 0
+    assert serving.select_next(w, 2.5, max_wait=2.0).rid == 0
+    assert serving.select_next(w[2:], 2.5, max_wait=2.0).rid == 2
+    assert serving.select_next([], 0.0) is None
