@@ -281,7 +281,8 @@ def run_cavity(binding, stream, n=1024, steps=20000):
 
 def run_precision(binding, stream, max_steps=60000, chunk=5000):
     """Storage precision on the Poiseuille channel 64 x 32 (u_max 0.01): run
-    to steady state (residual <= 1e-12, or max_steps) in each storage format,
+    to steady state (residual <= 1e-12, or max_steps) in each storage format
+    (16-bit: stochastic rounding, the default, and round-to-nearest),
     then the relative velocity error against the exact discrete steady state
     of the method, U(y) = 3 f y (H - y) - f with rho = 1 (it holds for the
     wall rule of Eq. feqnoslip, so the FP32 figure is rounding alone), and
@@ -296,8 +297,14 @@ def run_precision(binding, stream, max_steps=60000, chunk=5000):
     exact = parabola - f
     out = {"workload": "Poiseuille channel 64x32 (x-periodic, walls at "
                        "y = 0 and 31), u_max 0.01, run to residual 1e-12"}
-    for storage in ("f32", "f16", "bf16"):
-        d = problem_domain(binding, p, stream, storage)
+    for storage, rounding in (("f32", "nearest"), ("f16", "stochastic"),
+                              ("bf16", "stochastic"), ("f16", "nearest"),
+                              ("bf16", "nearest")):
+        ny_, nx_ = p.mask.shape
+        d = binding.Domain(nx_, ny_, p.periodic, p.force, stream=stream,
+                           storage=storage, rounding=rounding)
+        d.set_geometry(p.mask)
+        d.set_moments(p.rho, p.jx, p.jy)
         steps, res = 0, float("inf")
         while steps < max_steps:
             d.step(chunk)
@@ -308,7 +315,10 @@ def run_precision(binding, stream, max_steps=60000, chunk=5000):
         R, U, _ = d.moments()
         d.close()
         u = (U / R)[1:H, :]
-        out[storage] = {
+        key = storage if rounding == "stochastic" or storage == "f32" \
+            else storage + "_nearest"
+        out[key] = {
+            "rounding": rounding if storage != "f32" else "fp32",
             "steps": steps, "residual": res,
             "err_vs_exact_steady_state": float(
                 np.abs(u - exact[:, None]).max() / exact.max()),

@@ -63,6 +63,16 @@ extern "C" {
                               (12 B/node, 2 copies) */
 #define LBM_STORAGE_BF16 2 /* as bfloat16, unscaled (12 B/node, 2 copies) */
 
+/* Rounding of the 16-bit storage formats (FP32 storage ignores it).
+ * Stochastic rounding rounds each stored value up or down with probabilities
+ * that make its expected value exact, drawing the random bits from a counter-
+ * based hash of (column, row, field, step count): a run is reproducible bit
+ * for bit, and increments smaller than half a unit in the last place are not
+ * lost (under round-to-nearest a slowly converging flow stalls far from its
+ * steady state).  It is the default. */
+#define LBM_ROUND_STOCHASTIC 0
+#define LBM_ROUND_NEAREST 1
+
 /* Problem statement.  Zero-initialise before filling in. */
 typedef struct lbm_params {
   int64_t nx;         /* nodes along x, >= 1 */
@@ -72,7 +82,7 @@ typedef struct lbm_params {
   double fx;          /* body force, momentum added per node per step */
   double fy;
   int32_t storage;    /* LBM_STORAGE_F32, _F16 or _BF16 */
-  int32_t reserved;   /* must be 0 */
+  int32_t rounding;   /* LBM_ROUND_STOCHASTIC (0) or LBM_ROUND_NEAREST */
 } lbm_params;
 
 typedef struct lbm_ctx lbm_ctx;
@@ -163,6 +173,15 @@ int lbm_moments(lbm_ctx *ctx, double *rho, double *jx, double *jy);
 int lbm_get_state(lbm_ctx *ctx, void *drho, void *jx, void *jy);
 int lbm_set_state(lbm_ctx *ctx, const void *drho, const void *jx,
                   const void *jy);
+
+/*
+ * Steps the context has taken (lbm_step and batch steps), which seeds the
+ * stochastic rounding of 16-bit storage: a checkpoint of such a context
+ * saves it beside the state and a resume sets it again, so that the resumed
+ * run continues bit for bit.  Errors: LBM_E_INVAL (null, steps < 0).
+ */
+int lbm_step_count(const lbm_ctx *ctx, int64_t *steps);
+int lbm_set_step_count(lbm_ctx *ctx, int64_t steps);
 
 /*
  * Residual and mass of the last step run by lbm_step, over fluid nodes, with

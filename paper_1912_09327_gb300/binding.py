@@ -27,6 +27,10 @@ LBM_STORAGE_F16 = 1
 LBM_STORAGE_BF16 = 2
 STORAGE_NAMES = {"f32": LBM_STORAGE_F32, "f16": LBM_STORAGE_F16,
                  "bf16": LBM_STORAGE_BF16}
+LBM_ROUND_STOCHASTIC = 0
+LBM_ROUND_NEAREST = 1
+ROUNDING_NAMES = {"stochastic": LBM_ROUND_STOCHASTIC,
+                  "nearest": LBM_ROUND_NEAREST}
 # host dtype of the exact state transfers (bfloat16 as raw 16-bit words)
 STATE_DTYPE = {LBM_STORAGE_F32: np.float32, LBM_STORAGE_F16: np.float16,
                LBM_STORAGE_BF16: np.uint16}
@@ -43,7 +47,7 @@ class lbm_params(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int64), ("ny", ctypes.c_int64),
                 ("periodic_x", ctypes.c_int32), ("periodic_y", ctypes.c_int32),
                 ("fx", ctypes.c_double), ("fy", ctypes.c_double),
-                ("storage", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("storage", ctypes.c_int32), ("rounding", ctypes.c_int32)]
 
 
 _P = ctypes.POINTER(lbm_params)
@@ -59,6 +63,10 @@ _lib.lbm_set_moments.argtypes = [_vp, _vp, _vp, _vp]
 _lib.lbm_set_moments.restype = ctypes.c_int
 _lib.lbm_step.argtypes = [_vp, ctypes.c_int64]
 _lib.lbm_step.restype = ctypes.c_int
+_lib.lbm_step_count.argtypes = [_vp, _vp]
+_lib.lbm_step_count.restype = ctypes.c_int
+_lib.lbm_set_step_count.argtypes = [_vp, ctypes.c_int64]
+_lib.lbm_set_step_count.restype = ctypes.c_int
 _lib.lbm_set_variant.argtypes = [_vp, ctypes.c_int32]
 _lib.lbm_set_variant.restype = ctypes.c_int
 _lib.lbm_variant.argtypes = [_vp]
@@ -136,10 +144,13 @@ def _check(status, ctx=None):
 
 
 def make_params(nx, ny, periodic=(False, False), force=(0.0, 0.0),
-                storage=LBM_STORAGE_F32) -> lbm_params:
+                storage=LBM_STORAGE_F32,
+                rounding=LBM_ROUND_STOCHASTIC) -> lbm_params:
+    if isinstance(rounding, str):
+        rounding = ROUNDING_NAMES[rounding]
     return lbm_params(int(nx), int(ny), int(bool(periodic[0])),
                       int(bool(periodic[1])), float(force[0]), float(force[1]),
-                      int(storage), 0)
+                      int(storage), int(rounding))
 
 
 def _ptr(a):
@@ -179,6 +190,16 @@ def lbm_set_moments(ctx, rho, jx, jy) -> None:
 
 def lbm_step(ctx, nsteps: int) -> None:
     _check(_lib.lbm_step(ctx, int(nsteps)), ctx)
+
+
+def lbm_step_count(ctx) -> int:
+    n = ctypes.c_int64()
+    _check(_lib.lbm_step_count(ctx, ctypes.byref(n)), ctx)
+    return int(n.value)
+
+
+def lbm_set_step_count(ctx, steps: int) -> None:
+    _check(_lib.lbm_set_step_count(ctx, int(steps)), ctx)
 
 
 def lbm_set_variant(ctx, variant: int) -> None:
@@ -389,13 +410,15 @@ class Domain:
     a context.  Methods map one-to-one to the C calls."""
 
     def __init__(self, nx, ny, periodic=(False, False), force=(0.0, 0.0),
-                 device="cuda", stream=None, storage=LBM_STORAGE_F32):
+                 device="cuda", stream=None, storage=LBM_STORAGE_F32,
+                 rounding=LBM_ROUND_STOCHASTIC):
         import torch
         self.nx, self.ny = int(nx), int(ny)
         if isinstance(storage, str):
             storage = STORAGE_NAMES[storage]
         self.storage = int(storage)
-        self.params = make_params(nx, ny, periodic, force, self.storage)
+        self.params = make_params(nx, ny, periodic, force, self.storage,
+                                  rounding)
         nbytes = lbm_workspace_bytes(self.params)
         if nbytes == 0:
             raise LbmError(LBM_E_INVAL, "invalid domain parameters")
@@ -424,6 +447,12 @@ class Domain:
 
     def set_variant(self, v):
         lbm_set_variant(self.ctx, v)
+
+    def step_count(self):
+        return lbm_step_count(self.ctx)
+
+    def set_step_count(self, steps):
+        lbm_set_step_count(self.ctx, steps)
 
     def variant(self):
         return lbm_variant(self.ctx)

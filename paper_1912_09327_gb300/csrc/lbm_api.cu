@@ -30,7 +30,9 @@ bool params_ok(const lbm_params *p) {
          p->ny <= kMaxExtent &&
          (p->storage == LBM_STORAGE_F32 || p->storage == LBM_STORAGE_F16 ||
           p->storage == LBM_STORAGE_BF16) &&
-         p->reserved == 0 && isfinite(p->fx) && isfinite(p->fy);
+         (p->rounding == LBM_ROUND_STOCHASTIC ||
+          p->rounding == LBM_ROUND_NEAREST) &&
+         isfinite(p->fx) && isfinite(p->fy);
 }
 
 Layout make_layout(const lbm_params *p) {
@@ -150,6 +152,7 @@ int lbm_create(const lbm_params *p, void *dev_workspace, size_t workspace_bytes,
   c->stream = static_cast<cudaStream_t>(cuda_stream);
   c->cur = 0;
   c->variant = -1;
+  c->steps = 0;
   c->has_geometry = false;
   c->has_residual = false;
   c->n_fluid = 0;
@@ -305,9 +308,12 @@ int lbm_step(lbm_ctx *c, int64_t nsteps) {
   if (c->variant < 0)
     c->variant = lbmtau1::choose_variant(c->p.nx, c->p.ny, c->p.storage);
   a.variant = c->variant;
+  a.sr = c->p.storage != LBM_STORAGE_F32 &&
+         c->p.rounding == LBM_ROUND_STOCHASTIC;
   for (int64_t s = 0; s < nsteps; ++s) {
     a.src = c->f[c->cur];
     a.dst = c->f[1 - c->cur];
+    a.step = static_cast<uint32_t>(c->steps + s);
     cudaError_t e = lbmtau1::launch_step(a, s == nsteps - 1, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "step kernel launch");
     c->cur = 1 - c->cur;
@@ -317,6 +323,20 @@ int lbm_step(lbm_ctx *c, int64_t nsteps) {
       c->result, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "finalize kernel launch");
   c->has_residual = true;
+  c->steps += nsteps;
+  return LBM_OK;
+}
+
+int lbm_step_count(const lbm_ctx *c, int64_t *steps) {
+  if (!c || !steps) return LBM_E_INVAL;
+  *steps = c->steps;
+  return LBM_OK;
+}
+
+int lbm_set_step_count(lbm_ctx *c, int64_t steps) {
+  if (!c) return LBM_E_INVAL;
+  if (steps < 0) return fail(c, LBM_E_INVAL, "steps < 0");
+  c->steps = steps;
   return LBM_OK;
 }
 

@@ -48,7 +48,7 @@ BatchLayout batch_layout(int32_t capacity, int64_t max_tiles) {
   L.off_nitems = off;
   off += kAlign;
   L.off_counters = off;
-  off += align_up(sizeof(unsigned) * (kChunk + 1), kAlign);
+  off += align_up(sizeof(unsigned) * (kChunk + 3), kAlign);
   L.off_gather = off;
   off += align_up(sizeof(double) * 4 * static_cast<size_t>(capacity), kAlign);
   L.total = off;
@@ -63,7 +63,10 @@ struct lbm_batch {
   BatchMember *d_members;
   int4 *d_items;
   int *d_nitems;
-  unsigned *d_counters;  // [0, kChunk) graph steps, [kChunk] direct steps
+  unsigned *d_counters;  // [0, kChunk) graph steps, [kChunk] direct steps,
+                         // [kChunk + 1] batch clock, [kChunk + 2] done count
+  uint32_t clock;        // host mirror of the batch clock
+  bool clock_set;        // device clock and done count zeroed
   double *d_gather;      // 4 doubles per member: result sums and flag
   cudaStream_t stream;
   std::vector<lbm_ctx *> slots;
@@ -131,7 +134,9 @@ int upload(lbm_batch *b) {
     m.gx = (c->p.nx + tx - 1) / tx;
     m.nblocks = m.gx * ((c->p.ny + ty - 1) / ty);
     m.cur = c->cur;
-    m.pad = 0;
+    m.sr = c->p.storage != LBM_STORAGE_F32 &&
+           c->p.rounding == LBM_ROUND_STOCHASTIC;
+    m.step_base = c->steps - static_cast<int64_t>(b->clock);
   }
   if (b->items_dirty) {
     b->h_items.clear();
@@ -176,6 +181,8 @@ BatchLaunch launch_args(lbm_batch *b, unsigned *counter, int parity) {
   L.counter = counter;
   L.parity = parity;
   L.storage = b->storage;
+  L.clock = b->d_counters + kChunk + 1;
+  L.done = b->d_counters + kChunk + 2;
   return L;
 }
 
@@ -289,6 +296,8 @@ int lbm_batch_create(int32_t capacity, int64_t max_tiles, void *dev_workspace,
   b->d_counters = reinterpret_cast<unsigned *>(base + L.off_counters);
   b->d_gather = reinterpret_cast<double *>(base + L.off_gather);
   b->stream = static_cast<cudaStream_t>(cuda_stream);
+  b->clock = 0;
+  b->clock_set = false;
   b->slots.assign(capacity, nullptr);
   b->nitems = 0;
   b->storage = -1;
@@ -362,6 +371,12 @@ int lbm_batch_step(lbm_batch *b, int64_t nsteps) {
   if (nsteps == 0 || lbm_batch_members(b) == 0) return LBM_OK;
   int st = upload(b);
   if (st) return st;
+  if (!b->clock_set) {  // the batch clock and the done count start at zero
+    cudaError_t e = cudaMemsetAsync(b->d_counters + kChunk + 1, 0,
+                                    2 * sizeof(unsigned), b->stream);
+    if (e != cudaSuccess) return bcuda(b, e, "cudaMemsetAsync(clock)");
+    b->clock_set = true;
+  }
   int64_t s = 0;
   // first step direct (one-time kernel set-up stays outside any capture)
   for (; s < nsteps && s < 2; ++s) {
@@ -383,7 +398,9 @@ int lbm_batch_step(lbm_batch *b, int64_t nsteps) {
   for (lbm_ctx *c : b->packed) {
     c->cur ^= static_cast<int>(nsteps & 1);
     c->has_residual = true;
+    c->steps += nsteps;
   }
+  b->clock += static_cast<uint32_t>(nsteps);
   b->err[0] = '\0';
   return LBM_OK;
 }

@@ -37,6 +37,7 @@ struct lbm_ctx {
   cudaStream_t stream;
   int cur;              // copy holding the current state
   int variant;          // tile variant, chosen at the first step (-1 before)
+  int64_t steps;        // steps taken (seeds stochastic rounding)
   bool has_geometry;
   bool has_residual;
   int64_t n_fluid;

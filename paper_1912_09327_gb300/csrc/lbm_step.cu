@@ -163,6 +163,53 @@ __device__ __forceinline__ void store_vec(T *p, const float (&v)[kC],
   *reinterpret_cast<V *>(p) = u.v;
 }
 
+// ---- Stochastic rounding of the 16-bit formats ----
+// Random bits from a counter-based hash: the 32-bit finaliser of Appleby's
+// MurmurHash3 (a bijection of 32-bit words with full avalanche), applied to
+// the step count, then the row, then (column, field).
+__device__ __forceinline__ uint32_t fmix32(uint32_t h) {
+  h ^= h >> 16;
+  h *= 0x85ebca6bu;
+  h ^= h >> 13;
+  h *= 0xc2b2ae35u;
+  h ^= h >> 16;
+  return h;
+}
+
+// Two FP32 values to one packed pair, each rounded up or down at random with
+// the probability that makes its expected value exact (cvt.rs, sm_100
+// family); `lo` lands in the low half (the lower address).
+__device__ __forceinline__ uint32_t pack_sr(__half, float lo, float hi,
+                                            uint32_t bits) {
+  uint32_t d;
+  asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(bits));
+  return d;
+}
+__device__ __forceinline__ uint32_t pack_sr(__nv_bfloat16, float lo, float hi,
+                                            uint32_t bits) {
+  uint32_t d;
+  asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(bits));
+  return d;
+}
+
+// store_vec with stochastic rounding; `key` identifies (row, step, field) and
+// `x` is the first column (each pair of columns draws one hashed word).
+template <int kC, typename T>
+__device__ __forceinline__ void store_vec_sr(T *p, const float (&v)[kC],
+                                             float scale, uint32_t key,
+                                             uint32_t x) {
+  static_assert(kC % 2 == 0, "pairs of columns");
+  uint32_t w[kC / 2];
+#pragma unroll
+  for (int q = 0; q < kC / 2; ++q)
+    w[q] = pack_sr(T(), v[2 * q] * scale, v[2 * q + 1] * scale,
+                   fmix32(key + (x + 2u * q) * 0x9e3779b1u));
+  if constexpr (kC == 4)
+    *reinterpret_cast<uint2 *>(p) = make_uint2(w[0], w[1]);
+  else
+    *reinterpret_cast<uint32_t *>(p) = w[0];
+}
+
 // One source row as loaded: kC columns of raw fields and their node types.
 template <int kC>
 struct RawRow {
@@ -690,7 +737,38 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
         south_mx[j] = Tmx;
         south_my[j] = Tmy;
       }
-      if (owner) {
+      bool stored = false;
+      if constexpr (!std::is_same<T, float>::value) {
+        if (a.sr) {  // uniform across the warp
+          stored = true;
+          if (owner) {
+            T *dd = static_cast<T *>(a.dst.d);
+            T *dx = static_cast<T *>(a.dst.jx);
+            T *dy = static_cast<T *>(a.dst.jy);
+            const uint32_t xs = static_cast<uint32_t>(xb);
+            const uint32_t sk = fmix32(a.step);
+            // one key per (row, step); fields offset it by constants
+            auto row_key = [&](int64_t row) {
+              return fmix32(sk ^ (static_cast<uint32_t>(row) * 0x85ebca77u));
+            };
+            if (r - 1 >= y0) {
+              const uint32_t key = row_key(r - 1);
+              const int64_t o = (r - 1) * a.pitch + xb;
+              store_vec_sr<kC, T>(dd + o, od0, SS::kD, key, xs);
+              store_vec_sr<kC, T>(dx + o, ox0, SS::kJ, key + 0x632be5abu, xs);
+              store_vec_sr<kC, T>(dy + o, oy0, SS::kJ, key + 0xc6bc279au, xs);
+            }
+            if (r >= y0 && r < y1) {
+              const uint32_t key = row_key(r);
+              const int64_t o = r * a.pitch + xb;
+              store_vec_sr<kC, T>(dd + o, od1, SS::kD, key, xs);
+              store_vec_sr<kC, T>(dx + o, ox1, SS::kJ, key + 0x632be5abu, xs);
+              store_vec_sr<kC, T>(dy + o, oy1, SS::kJ, key + 0xc6bc279au, xs);
+            }
+          }
+        }
+      }
+      if (owner && !stored) {
         T *dd = static_cast<T *>(a.dst.d);
         T *dx = static_cast<T *>(a.dst.jx);
         T *dy = static_cast<T *>(a.dst.jy);
@@ -789,6 +867,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks)
   SolidSums *lut = reinterpret_cast<SolidSums *>(smem);
   __shared__ int s_item;
   build_solid_lut(lut);
+  // the batch clock: read by every block before the last block advances it
+  const unsigned clock = *b.clock;
   __syncthreads();
   const int n = *b.nitems;
   for (;;) {
@@ -814,7 +894,18 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks)
     a.partials = m.partials;
     a.flag = m.flag;
     a.storage = b.storage;
+    a.sr = m.sr;
+    a.step = static_cast<uint32_t>(m.step_base) + clock;
     step_tile<T, kC, kRows, kS, kReduce>(a, w.y, w.z, m.gx, lut, smem);
+  }
+  // the last block to finish advances the clock for the next launch
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(b.done, 1u) == gridDim.x - 1) {
+      *b.done = 0u;
+      *b.clock = clock + 1u;
+      __threadfence();
+    }
   }
 }
 

@@ -31,6 +31,8 @@ struct StepLaunch {
   unsigned int *flag;   // sticky instability flag (reduced steps only)
   int storage = kStorageF32;
   int variant = 0;      // tile variant (see choose_variant)
+  int sr = 0;           // 16-bit storage: stochastic rounding
+  uint32_t step = 0;    // the domain's step count (seeds the rounding)
 };
 
 // One member of a batch (see launch_batch): both field copies, the copy that
@@ -48,7 +50,8 @@ struct BatchMember {
   int64_t gx;        // block tiles along x for the batch's tile variant
   int64_t nblocks;   // block tiles of the member
   int cur;           // copy holding the state when the batch step starts
-  int pad;
+  int sr;            // 16-bit storage: stochastic rounding
+  int64_t step_base; // member's step count minus the batch clock
 };
 
 struct BatchLaunch {
@@ -58,6 +61,8 @@ struct BatchLaunch {
   unsigned int *counter;  // zeroed before the launch
   int parity;             // step index within the call, mod 2
   int storage;            // storage format shared by all members
+  unsigned int *clock;    // batch steps taken (advanced by each launch)
+  unsigned int *done;     // blocks finished in this launch (zero between)
 };
 
 // Tile variants: their number, the block tile size of variant v, and the

@@ -74,6 +74,40 @@ def test_batch_equals_each_alone(b, nsteps):
     batch.close()
 
 
+@pytest.mark.parametrize("fmt", ["f16", "bf16"])
+def test_batch_stochastic_rounding_equals_alone(b, fmt):
+    """16-bit storage with stochastic rounding: a member's random bits follow
+    its own step count (the batch clock advanced by each launch, offset per
+    member), so batched steps, graph chunks included, give every member the
+    state it reaches alone, bit for bit; also after a member stepped on its
+    own in between."""
+    probs = mixed_problems(6, seed=21)
+    import torch
+    stream = torch.cuda.Stream()
+    alone = []
+    for p in probs:
+        d = b.Domain.from_problem(p, storage=fmt)
+        d.step(5)
+        d.step(37)
+        alone.append(d.get_state())
+        d.close()
+    doms = [b.Domain.from_problem(p, stream=stream, storage=fmt) for p in probs]
+    batch = b.Batch(len(doms), 100000, stream=stream)
+    doms[0].step(5)                 # member 0 on its own first: 5
+    slots = [batch.add(d) for d in doms]
+    batch.step(5)                   # member 0 at 10, the others at 5
+    batch.remove(slots[0])
+    batch.step(32)                  # the others at 37 (graph chunks)
+    doms[0].step(27)                # member 0 on its own to 37
+    batch.add(doms[0])
+    batch.step(5)                   # everyone at 42
+    for d, want in zip(doms, alone):
+        assert d.step_count() == 42
+        for x, y in zip(d.get_state(), want):
+            assert np.array_equal(x.view(np.uint16), y.view(np.uint16))
+    batch.close()
+
+
 def test_batch_variants_are_identical_and_autotune(b):
     probs = mixed_problems(6, seed=11)
     import torch
