@@ -75,8 +75,8 @@ extern "C" {
 
 /* Problem statement.  Zero-initialise before filling in. */
 typedef struct lbm_params {
-  int64_t nx;         /* nodes along x, >= 1 */
-  int64_t ny;         /* nodes along y, >= 1 */
+  int64_t nx;         /* nodes along x, 1 .. 2^30 - 1 */
+  int64_t ny;         /* nodes along y, 1 .. 2^30 - 1 */
   int32_t periodic_x; /* nonzero: x wraps (e.g. the channel of Section 3) */
   int32_t periodic_y; /* nonzero: y wraps */
   double fx;          /* body force, momentum added per node per step */

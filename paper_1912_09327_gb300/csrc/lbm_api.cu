@@ -21,7 +21,7 @@ namespace {
 constexpr int64_t kPitchAlign = 32;           // nodes; rows start 128-B aligned
 constexpr size_t kAlign = 256;                // bytes; every workspace region
 constexpr int64_t kStagingNodes = 1 << 20;    // host-transfer chunk (nodes)
-constexpr int64_t kMaxExtent = int64_t(1) << 31;
+constexpr int64_t kMaxExtent = (int64_t(1) << 30) - 1;  // rows index in 32 bits
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 

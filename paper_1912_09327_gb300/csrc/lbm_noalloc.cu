@@ -52,7 +52,8 @@ extern "C" int lbm_step_noalloc(const float *drho_in, const float *jx_in,
   if (!drho_in || !jx_in || !jy_in || !drho_out || !jx_out || !jy_out ||
       !mask || !dev_sums || !dev_flags)
     return LBM_E_INVAL;
-  if (nx < 1 || ny < 1 || pitch < nx || pitch % 32 != 0)
+  if (nx < 1 || ny < 1 || nx >= (int64_t(1) << 30) || ny >= (int64_t(1) << 30) ||
+      pitch < nx || pitch % 32 != 0)
     return LBM_E_INVAL;
   const void *ptrs[7] = {drho_in, jx_in, jy_in, drho_out, jx_out, jy_out, mask};
   for (const void *p : ptrs)

@@ -448,17 +448,20 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
     unsigned pA6 = 0u, pB6 = 0u;  // solid bits (cols -1..kC) of rows r-2, r-1
     unsigned pfluidB = 0u;        // fluid bits of row r-1
 
-    const int64_t npairs = (y1 - y0 + 1) / 2 + 1;
-    const int64_t nrows = 2 * npairs;  // source rows y0 - 1 .. y0 - 2 + nrows
+    // Row indices in 32 bits: the launchers reject ny >= 2^30.
+    const int ty0 = static_cast<int>(y0), ty1 = static_cast<int>(y1);
+    const int tny = static_cast<int>(a.ny);
+    const int npairs = (ty1 - ty0 + 1) / 2 + 1;
+    const int nrows = 2 * npairs;  // source rows y0 - 1 .. y0 - 2 + nrows
     // source row of ring index i: -1 for a solid row beyond a wall-less edge
-    auto source_row = [&](int64_t i) -> int64_t {
-      int64_t r = y0 - 1 + i;
-      if (r >= 0 && r < a.ny) return r;
-      return a.periodic_y ? wrap_index(r, a.ny) : -1;
+    auto source_row = [&](int i) -> int {
+      const int r = ty0 - 1 + i;
+      if (r >= 0 && r < tny) return r;
+      return a.periodic_y ? static_cast<int>(wrap_index(r, tny)) : -1;
     };
-    auto issue = [&](int64_t i) {  // lane 0 only
-      const int64_t r = source_row(i);
-      const int st = static_cast<int>(i % kS);
+    auto issue = [&](int i) {  // lane 0 only
+      const int r = source_row(i);
+      const int st = static_cast<int>(static_cast<unsigned>(i) % kS);
       uint64_t *bar = bars + st;
       if (r < 0) {  // solid row: nothing to copy, but the phase still completes
         mbar_arrive(bar);
@@ -467,7 +470,7 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
       unsigned char *dst = stages + st * St::kBytes;
       unsigned char *dmask = dst + 3 * St::kFieldBytes;
       if (interior) {  // the whole window lies in the row
-        const int64_t off = r * a.pitch + ws;
+        const int64_t off = static_cast<int64_t>(r) * a.pitch + ws;
         mbar_expect_tx(bar, 3 * St::kFieldBytes + St::kMaskBytes);
         bulk_copy(dst, static_cast<const T *>(a.src.d) + off, St::kFieldBytes,
                   bar);
@@ -487,10 +490,11 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
       const uint32_t mbytes = static_cast<uint32_t>(k1 - k0);
       mbar_expect_tx(bar, 3 * fbytes + mbytes + (wrap_l ? 64u : 0u) +
                               (wrap_r ? 64u : 0u));
-      const T *src[3] = {static_cast<const T *>(a.src.d) + r * a.pitch,
-                         static_cast<const T *>(a.src.jx) + r * a.pitch,
-                         static_cast<const T *>(a.src.jy) + r * a.pitch};
-      const uint8_t *mrow = a.mask + r * a.pitch;
+      const int64_t rp = static_cast<int64_t>(r) * a.pitch;
+      const T *src[3] = {static_cast<const T *>(a.src.d) + rp,
+                         static_cast<const T *>(a.src.jx) + rp,
+                         static_cast<const T *>(a.src.jy) + rp};
+      const uint8_t *mrow = a.mask + rp;
       const int64_t foff = (c0 - ws) * static_cast<int64_t>(sizeof(T));
 #pragma unroll
       for (int f = 0; f < 3; ++f)
@@ -511,7 +515,7 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
       }
     };
     // ring row i -> registers; false when the copy did not arrive in time
-    auto fetch = [&](int64_t i, RawRow<kC> &o) -> bool {
+    auto fetch = [&](int i, RawRow<kC> &o) -> bool {
       if (source_row(i) < 0) {
 #pragma unroll
         for (int j = 0; j < kC; ++j) o.d[j] = o.jx[j] = o.jy[j] = 0.f;
@@ -519,8 +523,9 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
         o.fluid = 0u;
         return true;
       }
-      const int st = static_cast<int>(i % kS);
-      const bool ok = mbar_wait(bars + st, static_cast<uint32_t>((i / kS) & 1));
+      const unsigned ui = static_cast<unsigned>(i);
+      const int st = static_cast<int>(ui % kS);
+      const bool ok = mbar_wait(bars + st, (ui / kS) & 1u);
       const unsigned char *src = stages + st * St::kBytes;
       const T *fd = reinterpret_cast<const T *>(src);
       const T *fx_ = reinterpret_cast<const T *>(src + St::kFieldBytes);
@@ -564,7 +569,7 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
       }
       return ok;
     };
-    int64_t issued = 0;
+    int issued = 0;
     if (lane == 0) {
       for (int st = 0; st < kS; ++st) mbar_init(bars + st);
       fence_async_shared();
@@ -573,12 +578,12 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
     issued = __shfl_sync(kFull, issued, 0);
     __syncwarp();
     bool aborted = false;
-    int64_t consumed = 0;
-    for (int64_t k = 0; k < npairs; ++k) {
+    int consumed = 0;
+    for (int k = 0; k < npairs; ++k) {
       consumed = 2 * k;
-      const int64_t r = y0 - 1 + 2 * k;  // S = (r, r+1)
-      const bool row0 = r - 1 >= y0;        // output row r - 1 is in the tile
-      const bool row1 = r >= y0 && r < y1;  // output row r is in the tile
+      const int r = ty0 - 1 + 2 * k;  // S = (r, r+1)
+      const bool row0 = r - 1 >= ty0;         // output row r - 1 is in the tile
+      const bool row1 = r >= ty0 && r < ty1;  // output row r is in the tile
       RawRow<kC> ra, rb;
       bool ok = fetch(2 * k, ra);
       ok = fetch(2 * k + 1, rb) && ok;
@@ -748,19 +753,19 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
             const uint32_t xs = static_cast<uint32_t>(xb);
             const uint32_t sk = fmix32(a.step);
             // one key per (row, step); fields offset it by constants
-            auto row_key = [&](int64_t row) {
+            auto row_key = [&](int row) {
               return fmix32(sk ^ (static_cast<uint32_t>(row) * 0x85ebca77u));
             };
-            if (r - 1 >= y0) {
+            if (row0) {
               const uint32_t key = row_key(r - 1);
-              const int64_t o = (r - 1) * a.pitch + xb;
+              const int64_t o = static_cast<int64_t>(r - 1) * a.pitch + xb;
               store_vec_sr<kC, T>(dd + o, od0, SS::kD, key, xs);
               store_vec_sr<kC, T>(dx + o, ox0, SS::kJ, key + 0x632be5abu, xs);
               store_vec_sr<kC, T>(dy + o, oy0, SS::kJ, key + 0xc6bc279au, xs);
             }
-            if (r >= y0 && r < y1) {
+            if (row1) {
               const uint32_t key = row_key(r);
-              const int64_t o = r * a.pitch + xb;
+              const int64_t o = static_cast<int64_t>(r) * a.pitch + xb;
               store_vec_sr<kC, T>(dd + o, od1, SS::kD, key, xs);
               store_vec_sr<kC, T>(dx + o, ox1, SS::kJ, key + 0x632be5abu, xs);
               store_vec_sr<kC, T>(dy + o, oy1, SS::kJ, key + 0xc6bc279au, xs);
@@ -772,14 +777,14 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
         T *dd = static_cast<T *>(a.dst.d);
         T *dx = static_cast<T *>(a.dst.jx);
         T *dy = static_cast<T *>(a.dst.jy);
-        if (r - 1 >= y0) {
-          const int64_t o = (r - 1) * a.pitch + xb;
+        if (row0) {
+          const int64_t o = static_cast<int64_t>(r - 1) * a.pitch + xb;
           store_vec<kC, T>(dd + o, od0, SS::kD);
           store_vec<kC, T>(dx + o, ox0, SS::kJ);
           store_vec<kC, T>(dy + o, oy0, SS::kJ);
         }
-        if (r >= y0 && r < y1) {
-          const int64_t o = r * a.pitch + xb;
+        if (row1) {
+          const int64_t o = static_cast<int64_t>(r) * a.pitch + xb;
           store_vec<kC, T>(dd + o, od1, SS::kD);
           store_vec<kC, T>(dx + o, ox1, SS::kJ);
           store_vec<kC, T>(dy + o, oy1, SS::kJ);
@@ -802,9 +807,10 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
     if (aborted) {
       if (lane == 0) atomicOr(a.flag, kFlagCopyTimeout);
       // let every copy still in flight land before the block exits
-      for (int64_t i = consumed; i < issued; ++i) {
+      for (int i = consumed; i < issued; ++i) {
         if (source_row(i) < 0) continue;
-        mbar_wait(bars + i % kS, static_cast<uint32_t>((i / kS) & 1));
+        const unsigned ui = static_cast<unsigned>(i);
+        mbar_wait(bars + ui % kS, (ui / kS) & 1u);
       }
     }
     // release the barriers so the ring can serve another tile
@@ -1260,6 +1266,8 @@ int choose_variant(int64_t nx, int64_t ny, int storage) {
 }
 
 cudaError_t launch_step(const StepLaunch &a, bool reduce, cudaStream_t s) {
+  if (a.ny >= (int64_t(1) << 30) || a.nx >= (int64_t(1) << 30))
+    return cudaErrorInvalidValue;  // the tile loop indexes rows in 32 bits
   switch (a.storage) {
     case kStorageF16: return launch_step_t<__half>(a, reduce, s);
     case kStorageBF16: return launch_step_t<__nv_bfloat16>(a, reduce, s);
