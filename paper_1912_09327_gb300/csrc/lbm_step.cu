@@ -690,24 +690,25 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
         const float2 dO = make_float2(pd[j], ra.d[j]);
         const float2 jxO = make_float2(pjx[j], ra.jx[j]);
         const float2 jyO = make_float2(pjy[j], ra.jy[j]);
-        float2 S0 = bc(0.f), Sx = bc(0.f), Sy = bc(0.f);
+        // the momentum increments; solid neighbours add their wall terms in
+        // place below (nothing to add, and no zero terms, without solids)
+        float2 dn = acc_dd;
+        float2 incx = fma2(w1_6, add(sub(zpx[j], jxO), sub(zx[C], jxO)),
+                           add(acc_mx, F2x));
+        float2 incy = fma2(half, add(sub(zpy[j], jyO), sub(zy[C], jyO)),
+                           add(acc_my, F2y));
         if (any_solid) {
           const unsigned c0 = ((pA6 >> j) & 7u) | (((pB6 >> j) & 7u) << 3) |
                               (((A6 >> j) & 7u) << 6);
           const unsigned c1 = ((pB6 >> j) & 7u) | (((A6 >> j) & 7u) << 3) |
                               (((B6 >> j) & 7u) << 6);
           const SolidSums e0 = lut[c0], e1 = lut[c1];
-          S0 = make_float2(e0.s0, e1.s0);
-          Sx = make_float2(e0.sx, e1.sx);
-          Sy = make_float2(e0.sy, e1.sy);
+          dn = fma2(dO, make_float2(e0.s0, e1.s0), dn);
+          incx = fma2(dO, make_float2(e0.sx, e1.sx), incx);
+          incy = fma2(dO, make_float2(e0.sy, e1.sy), incy);
         }
-        const float2 dn = fma2(dO, S0, acc_dd);
-        const float2 mxn = add(
-            jxO, fma2(dO, Sx, fma2(w1_6, add(sub(zpx[j], jxO), sub(zx[C], jxO)),
-                                   add(acc_mx, F2x))));
-        const float2 myn = add(
-            jyO, fma2(dO, Sy, fma2(half, add(sub(zpy[j], jyO), sub(zy[C], jyO)),
-                                   add(acc_my, F2y))));
+        const float2 mxn = add(jxO, incx);
+        const float2 myn = add(jyO, incy);
         const bool f0 = (pfluidB >> j) & 1u, f1 = (ra.fluid >> j) & 1u;
         od0[j] = f0 ? dn.x : dO.x;
         ox0[j] = f0 ? mxn.x : jxO.x;
@@ -730,10 +731,18 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
           const float2 ux = mul(mxn, irn), uy = mul(myn, irn);
           const float2 nn = fma2(dux, dux, mul(duy, duy));
           const float2 dd2 = fma2(ux, ux, mul(uy, uy));
-          rs_num = add(rs_num, make_float2(v0 ? nn.x : 0.f, v1 ? nn.y : 0.f));
-          rs_den = add(rs_den, make_float2(v0 ? dd2.x : 0.f, v1 ? dd2.y : 0.f));
-          rs_mass = add(rs_mass, make_float2(v0 ? dn.x : 0.f, v1 ? dn.y : 0.f));
-          rmin = fminf(rmin, fminf(v0 ? rn.x : 1.f, v1 ? rn.y : 1.f));
+          if (v0) {
+            rs_num.x += nn.x;
+            rs_den.x += dd2.x;
+            rs_mass.x += dn.x;
+            rmin = fminf(rmin, rn.x);
+          }
+          if (v1) {
+            rs_num.y += nn.y;
+            rs_den.y += dd2.y;
+            rs_mass.y += dn.y;
+            rmin = fminf(rmin, rn.y);
+          }
         }
         // carry to the next pair
         same_dd[j] = Sdd.y;
