@@ -61,6 +61,7 @@ def parse_args(argv=None):
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--batched-domains", type=int, default=512)
     ap.add_argument("--batched-steps", type=int, default=2000)
+    ap.add_argument("--batched-plain-steps", type=int, default=200)
     ap.add_argument("--serving-requests", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args(argv)
@@ -618,10 +619,11 @@ def main(argv=None):
         line["precision"] = run_precision(binding, stream)
     if rank == 0 and not args.no_batched:
         line["batched"] = run_batched(binding, args.batched_domains,
-                                      args.batched_steps)
-        line["batched_f16"] = run_batched(binding, args.batched_domains,
-                                          args.batched_steps, plain_steps=100,
-                                          storage="f16")
+                                      args.batched_steps,
+                                      plain_steps=args.batched_plain_steps)
+        line["batched_f16"] = run_batched(
+            binding, args.batched_domains, args.batched_steps,
+            plain_steps=max(1, args.batched_plain_steps // 2), storage="f16")
     if rank == 0 and not args.no_serving:
         line["serving"] = run_serving(args.serving_requests)
     if rank == 0 and not args.no_cpu_baseline:
