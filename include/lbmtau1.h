@@ -288,6 +288,7 @@ int lbm_batch_step(lbm_batch *b, int64_t nsteps);
  * bit-identical states. */
 int32_t lbm_variant_count(void);
 int lbm_batch_set_variant(lbm_batch *b, int32_t variant);
+int32_t lbm_batch_variant(const lbm_batch *b);
 
 /* Block tiles of an nx x ny domain under tile variant `variant`, or the
  * largest count over all variants for variant -1 (the bound to size a batch
@@ -301,7 +302,6 @@ int64_t lbm_tile_count(int64_t nx, int64_t ny, int32_t variant);
  * cols_per_lane may be NULL.  Errors: LBM_E_INVAL. */
 int lbm_variant_tile(int32_t variant, int64_t *tile_x, int64_t *tile_y,
                      int32_t *cols_per_lane);
-int32_t lbm_batch_variant(const lbm_batch *b);
 
 /* Autotuner: times steps_per_variant (even, >= 2) batch steps, plus two
  * warm-up steps, with every tile variant and keeps the fastest.  These are

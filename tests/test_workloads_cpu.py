@@ -89,3 +89,16 @@ def test_serving_admission_order():
     assert serving.select_next(w, 2.5, max_wait=2.0).rid == 0
     assert serving.select_next(w[2:], 2.5, max_wait=2.0).rid == 2
     assert serving.select_next([], 0.0) is None
+
+
+def test_serving_batch_variant_model():
+    """The service's tile variant for a batch: least padded tile work.  Many
+    64 x 64 domains fit short 8-row warp tiles; one 4096^2 domain wastes
+    little in the tall default tiles, which march fewer halo rows."""
+    from paper_1912_09327_gb300 import binding, serving
+    small = serving.choose_batch_variant([(64, 64)] * 20)
+    tx, ty, cols = binding.lbm_variant_tile(small)
+    assert ty == 32 and cols == 4
+    big = serving.choose_batch_variant([(4096, 4096)])
+    assert binding.lbm_variant_tile(big)[1] == 256
+    assert 0 <= serving.choose_batch_variant([(1, 1)]) < binding.lbm_variant_count()
