@@ -423,10 +423,10 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
   const int m_lane = static_cast<int>(ws - m0) + c_lane;
   const float fx = a.fx, fy = a.fy;
   const float2 F2x = bc(fx), F2y = bc(fy), F22y = bc(2.0f * fy);
-  const float2 one = bc(1.0f), c3 = bc(3.0f), cm15 = bc(-1.5f), c9 = bc(9.0f);
-  const float2 w1_9 = bc(k1_9), wm1_9 = bc(-k1_9), w1_36 = bc(k1_36),
-               wm1_36 = bc(-k1_36), w1_12 = bc(k1_12), w1_3 = bc(k1_3),
-               w4_9 = bc(k4_9), w1_6 = bc(k1_6), half = bc(0.5f);
+  const float2 one = bc(1.0f), c3 = bc(3.0f), cm15 = bc(-1.5f);
+  const float2 w1_9 = bc(k1_9), w1_36 = bc(k1_36), w1_12 = bc(k1_12),
+               w1_3 = bc(k1_3), w4_9 = bc(k4_9), w1_6 = bc(k1_6),
+               wm1_6 = bc(-k1_6), half = bc(0.5f), quarter = bc(0.25f);
 
   float2 rs_num = bc(0.f), rs_den = bc(0.f), rs_mass = bc(0.f);
   float rmin = 1.0f;
@@ -598,10 +598,12 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
       }
       issued = __shfl_sync(kFull, issued, 0);
 
-      // Per-node quantities of S, own columns at index j + 1.
-      float2 df[kC + 2], zx[kC + 2], zy[kC + 2], A[kC + 2], G[kC + 2],
-          X[kC + 2];
-      float2 B[kC], R0[kC], ir[kC];
+      // Per-node quantities of S, own columns at index j + 1, pre-scaled by
+      // the lattice weights they meet (K = (delta + A) / 9, G / 36, X / 36
+      // with A = 3 Pxx - 1.5 Pyy, G = delta + 3 tr Pi, X = 9 Pxy), so that
+      // each neighbour combination below is a sum or a difference.
+      float2 K[kC + 2], zx[kC + 2], zy[kC + 2], G[kC + 2], X[kC + 2];
+      float2 P[kC], R0[kC], ir[kC];
 #pragma unroll
       for (int j = 0; j < kC; ++j) {
         const bool sa = (ra.solid >> j) & 1u, sb = (rb.solid >> j) & 1u;
@@ -617,13 +619,12 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
         const float2 pxx = mul(t, mx), pxy = mul(t, my);
         const float2 pyy = mul(mul(my, my), irj);
         const float2 tr = add(pxx, pyy);
-        df[j + 1] = dfj;
         zx[j + 1] = zxj;
         zy[j + 1] = zyj;
-        A[j + 1] = fma2(c3, pxx, mul(cm15, pyy));
-        B[j] = fma2(c3, pyy, mul(cm15, pxx));
-        G[j + 1] = fma2(c3, tr, dfj);
-        X[j + 1] = mul(c9, pxy);
+        K[j + 1] = fma2(w1_9, dfj, fma2(w1_3, pxx, mul(wm1_6, pyy)));
+        P[j] = fma2(c3, pyy, fma2(cm15, pxx, dfj));  // delta + 3 Pyy - 1.5 Pxx
+        G[j + 1] = fma2(w1_12, tr, mul(w1_36, dfj));
+        X[j + 1] = mul(quarter, pxy);
         R0[j] = fma2(cm15, tr, make_float2(ra.d[j], rb.d[j]));
         ir[j] = irj;
       }
@@ -633,10 +634,9 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
   q[0].y = __shfl_up_sync(kFull, q[kC].y, 1);                        \
   q[kC + 1].x = __shfl_down_sync(kFull, q[1].x, 1);                  \
   q[kC + 1].y = __shfl_down_sync(kFull, q[1].y, 1);
-      LBM_HALO(df)
+      LBM_HALO(K)
       LBM_HALO(zx)
       LBM_HALO(zy)
-      LBM_HALO(A)
       LBM_HALO(G)
       LBM_HALO(X)
 #undef LBM_HALO
@@ -659,27 +659,24 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
         const float2 mys = add(add(zy[L], zy[R]), F22y);
         const float2 hx = add(sub(zx[L], zx[C]), sub(zx[R], zx[C]));  // exact
         const float2 hy = add(sub(zy[L], zy[C]), sub(zy[R], zy[C]));
-        const float2 P = add(df[C], B[j]);
-        const float2 Q = mul(c3, add(zy[C], F2y));
-        const float2 GmX = sub(Gs, Xd), GpX = add(Gs, Xd);
-        // S as the row pair above output rows (r-1, r): NW, N, NE
-        const float2 Ndd = fma2(w1_9, sub(P, Q),
-                                mul(w1_36, fma2(c3, sub(mxd, mys), GmX)));
-        const float2 Nmx = fma2(w1_36, sub(Gd, Xs), mul(w1_12, sub(hx, myd)));
-        const float2 Nmy =
-            fma2(wm1_9, P, fma2(wm1_36, GmX, mul(w1_12, sub(hy, mxd))));
+        // S as the row pair above output rows (r-1, r), N: NW, N, NE, and
+        // below them (r+1, r+2), T: SW, S, SE.  The two share their terms
+        // up to signs:
+        //   U = P/9 + Gs + mxd/12,  V = (zy_C + Fy)/3 + Xd + mys/12,
+        //   Y = Xd + hy/12,  U' = Gd + hx/12,  V' = Xs + myd/12,
+        //   N = (U - V, U' - V', Y - U),  T = (U + V, U' + V', Y + U)
+        // for (delta, jx, jy).
+        const float2 U = fma2(w1_9, P[j], fma2(w1_12, mxd, Gs));
+        const float2 V = fma2(w1_3, add(zy[C], F2y), fma2(w1_12, mys, Xd));
+        const float2 Y = fma2(w1_12, hy, Xd);
+        const float2 Up = fma2(w1_12, hx, Gd), Vp = fma2(w1_12, myd, Xs);
+        const float2 Ndd = sub(U, V), Tdd = add(U, V);
+        const float2 Nmx = sub(Up, Vp), Tmx = add(Up, Vp);
+        const float2 Nmy = sub(Y, U), Tmy = add(Y, U);
         // S as the own rows of outputs (r, r+1): W, O, E
-        const float2 Sdd = fma2(w4_9, R0[j],
-                                mul(w1_9, fma2(c3, mxd, add(add(df[L], df[R]),
-                                                            add(A[L], A[R])))));
-        const float2 Smx = fma2(w1_9, add(sub(df[L], df[R]), sub(A[L], A[R])),
-                                mul(w1_3, hx));
-        // S as the row pair below outputs (r+1, r+2): SW, S, SE
-        const float2 Tdd = fma2(w1_9, add(P, Q),
-                                mul(w1_36, fma2(c3, add(mxd, mys), GpX)));
-        const float2 Tmx = fma2(w1_36, add(Gd, Xs), mul(w1_12, add(hx, myd)));
-        const float2 Tmy =
-            fma2(w1_9, P, fma2(w1_36, GpX, mul(w1_12, add(hy, mxd))));
+        const float2 Sdd =
+            fma2(w4_9, R0[j], fma2(w1_3, mxd, add(K[L], K[R])));
+        const float2 Smx = fma2(w1_3, hx, sub(K[L], K[R]));
 
         // Complete output rows (r-1, r) of column j.
         const float2 acc_dd =
