@@ -717,17 +717,18 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
           const bool col = (out_cols >> j) & 1u;
           const bool v0 = f0 && col && row0;
           const bool v1 = f1 && col && row1;
-          // u_new - u_old = ((j_n - j_o) + (j_n d_o - j_o d_n)) / (rho_n rho_o)
+          // u_new - u_old = ((j_n - j_o) - u_o (d_n - d_o)) / rho_n: the
+          // step's own changes, no cancellation between two O(|u|) values
           const float2 rn = add(dn, one);
           const float2 irn =
               make_float2(__fdividef(1.0f, rn.x), __fdividef(1.0f, rn.y));
+          const float2 irn2 = mul(irn, irn);
           const float2 iro = make_float2(pir[j], ir[j].x);
-          const float2 sc = mul(irn, iro);
-          const float2 dux = mul(add(sub(mxn, jxO), sub(mul(mxn, dO), mul(jxO, dn))), sc);
-          const float2 duy = mul(add(sub(myn, jyO), sub(mul(myn, dO), mul(jyO, dn))), sc);
-          const float2 ux = mul(mxn, irn), uy = mul(myn, irn);
-          const float2 nn = fma2(dux, dux, mul(duy, duy));
-          const float2 dd2 = fma2(ux, ux, mul(uy, uy));
+          const float2 mdd = sub(dO, dn);
+          const float2 ex = fma2(mul(jxO, iro), mdd, sub(mxn, jxO));
+          const float2 ey = fma2(mul(jyO, iro), mdd, sub(myn, jyO));
+          const float2 nn = mul(fma2(ex, ex, mul(ey, ey)), irn2);
+          const float2 dd2 = mul(fma2(mxn, mxn, mul(myn, myn)), irn2);
           if (v0) {
             rs_num.x += nn.x;
             rs_den.x += dd2.x;
