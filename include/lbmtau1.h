@@ -257,7 +257,8 @@ void lbm_destroy(lbm_ctx *ctx);
 typedef struct lbm_batch lbm_batch;
 
 /* Device workspace of a batch of up to `capacity` members whose block tiles
- * number at most `max_tiles` in total; 0 when the arguments are invalid. */
+ * number at most `max_tiles` in total (< 2^29); 0 when the arguments are
+ * invalid. */
 size_t lbm_batch_workspace_bytes(int32_t capacity, int64_t max_tiles);
 
 /* Creates a batch over a caller-owned device workspace (256-byte aligned) on

@@ -53,7 +53,9 @@ Layout make_layout(const lbm_params *p) {
   // bulk row copies may read up to 16 bytes past a row's end; pad the plane
   off += align_up(plane + kAlign, kAlign);
   L.off_partials = off;
-  off += align_up(static_cast<size_t>(L.nblocks) * 3 * sizeof(double), kAlign);
+  off += align_up(static_cast<size_t>(L.nblocks) * lbmtau1::kTileWarps * 3 *
+                      sizeof(double),
+                  kAlign);
   L.off_result = off;
   off += kAlign;
   L.off_staging = off;

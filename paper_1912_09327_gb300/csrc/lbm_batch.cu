@@ -44,7 +44,9 @@ BatchLayout batch_layout(int32_t capacity, int64_t max_tiles) {
   L.off_members = off;
   off += align_up(sizeof(BatchMember) * static_cast<size_t>(capacity), kAlign);
   L.off_items = off;
-  off += align_up(sizeof(int4) * static_cast<size_t>(max_tiles), kAlign);
+  off += align_up(sizeof(int4) * static_cast<size_t>(max_tiles) *
+                      lbmtau1::kTileWarps,
+                  kAlign);
   L.off_nitems = off;
   off += kAlign;
   L.off_counters = off;
@@ -143,15 +145,21 @@ int upload(lbm_batch *b) {
     for (int i = 0; i < n; ++i) {
       const BatchMember &m = b->h_members[i];
       const int64_t gy = m.nblocks / m.gx;
+      // every warp tile of every block tile (vertical neighbours next to
+      // each other, for the rows they share)
       for (int64_t by = 0; by < gy; ++by)
         for (int64_t bx = 0; bx < m.gx; ++bx)
-          b->h_items.push_back(make_int4(i, static_cast<int>(bx),
-                                         static_cast<int>(by), 0));
+          for (int w = 0; w < lbmtau1::kTileWarps; ++w)
+            b->h_items.push_back(make_int4(i, static_cast<int>(bx),
+                                           static_cast<int>(by), w));
     }
-    if (static_cast<int64_t>(b->h_items.size()) > b->max_tiles)
+    const int64_t tiles =
+        static_cast<int64_t>(b->h_items.size()) / lbmtau1::kTileWarps;
+    if (tiles > b->max_tiles)
       return bfail(b, LBM_E_WORKSPACE,
-                   "batch needs %zu tiles, its workspace holds %lld",
-                   b->h_items.size(), static_cast<long long>(b->max_tiles));
+                   "batch needs %lld tiles, its workspace holds %lld",
+                   static_cast<long long>(tiles),
+                   static_cast<long long>(b->max_tiles));
     b->nitems = static_cast<int>(b->h_items.size());
     if (b->nitems) {
       cudaError_t e = cudaMemcpyAsync(b->d_items, b->h_items.data(),
@@ -247,7 +255,7 @@ int graph_chunk(lbm_batch *b) {
 extern "C" {
 
 size_t lbm_batch_workspace_bytes(int32_t capacity, int64_t max_tiles) {
-  if (capacity < 1 || max_tiles < 1 || max_tiles > (int64_t(1) << 31) - 1)
+  if (capacity < 1 || max_tiles < 1 || max_tiles > (int64_t(1) << 29) - 1)
     return 0;
   return batch_layout(capacity, max_tiles).total;
 }

@@ -21,15 +21,18 @@
 
 namespace {
 
-// Largest step launch the scratch can serve, in thread blocks; with the
-// widest tile variant that is about 2 * 10^9 nodes (about 10^9 with the
-// narrowest).
+// Largest step launch the scratch can serve, in thread blocks (block tiles);
+// the tile variant chosen for a domain makes that about 10^8 nodes for the
+// short tiles small domains get and 2 * 10^9 for the tall ones of large
+// domains.
 constexpr int64_t kNoAllocMaxBlocks = int64_t(1) << 16;
+constexpr int64_t kNoAllocPartials = kNoAllocMaxBlocks * lbmtau1::kTileWarps;
 constexpr int kMaxDevices = 64;
 
-// Per-block partial triples, then one slot whose low 4 bytes hold the flag.
+// Per-warp-tile partial triples (6 MB), then one slot whose low 4 bytes
+// hold the flag.
 static __device__ __align__(256) double
-    g_step_scratch[3 * kNoAllocMaxBlocks + 1];
+    g_step_scratch[3 * kNoAllocPartials + 1];
 
 std::once_flag g_setup_once[kMaxDevices];
 double *g_scratch_addr[kMaxDevices];
@@ -74,7 +77,7 @@ extern "C" int lbm_step_noalloc(const float *drho_in, const float *jx_in,
   });
   if (g_setup_status[dev] != cudaSuccess) return LBM_E_CUDA;
   double *partials = g_scratch_addr[dev];
-  unsigned *flag = reinterpret_cast<unsigned *>(partials + 3 * kNoAllocMaxBlocks);
+  unsigned *flag = reinterpret_cast<unsigned *>(partials + 3 * kNoAllocPartials);
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
 
   // The array keeps the previous call's contents: the flag must start at

@@ -58,7 +58,7 @@ namespace lbmtau1 {
 namespace {
 
 constexpr int kLanes = 32;
-constexpr int kWarps = 4;                     // warps per block, stacked in y
+constexpr int kWarps = kTileWarps;            // warps per block, stacked in y
 constexpr int kThreads = kWarps * kLanes;
 constexpr unsigned kFull = 0xffffffffu;
 
@@ -368,13 +368,15 @@ __host__ __device__ constexpr int smem_bytes() {
          kWarps * ring_bytes<T, kC, kS>();
 }
 
-// One block tile (bx, by) of a step: kWarps warp tiles of (30 kC) columns x
-// kRows rows stacked vertically.  `gx` is the number of tiles along x (for the
-// index of the block's reduction partial).  Every thread of the block calls it.
+// One warp tile of a step: warp w (0 .. kWarps - 1, stacked in y) of block
+// tile (bx, by), (30 kC) columns x kRows rows.  `gx` is the number of block
+// tiles along x (for the index of the warp's reduction partial); `slot` is
+// the calling warp's place in its block, which owns a shared-memory ring.
+// Every lane of the warp calls it; no other warp takes part.
 template <typename T, int kC, int kRows, int kS, bool kReduce>
 __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
-                                          int64_t by, int64_t gx,
-                                          const SolidSums *lut,
+                                          int64_t by, int w, int slot,
+                                          int64_t gx, const SolidSums *lut,
                                           unsigned char *smem) {
   static_assert(kRows % 2 == 0, "rows per warp must be even");
   static_assert(kS >= 4 && kS % 2 == 0 && kS <= 16, "ring stages");
@@ -383,10 +385,9 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
   using SS = Storage<T>;
 
   const int lane = threadIdx.x & (kLanes - 1);
-  const int warp = threadIdx.x / kLanes;
   const int64_t x0 = bx * kTile;
   const int64_t xb = x0 - kC + static_cast<int64_t>(kC) * lane;
-  const int64_t y0 = (by * kWarps + warp) * kRows;
+  const int64_t y0 = (by * kWarps + w) * kRows;
   const int64_t y1 = min(y0 + kRows, a.ny);
   const bool owner = lane >= 1 && lane <= kLanes - 2 && xb < a.nx;
   // columns of this lane that are outputs inside the domain (reductions)
@@ -416,7 +417,7 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
   if (wrap_r && xb <= a.nx && a.nx < xb + kC)          // column nx
     wrap_col = static_cast<int>(a.nx - xb);
   unsigned char *ring =
-      smem + 512 * sizeof(SolidSums) + warp * ring_bytes<T, kC, kS>();
+      smem + 512 * sizeof(SolidSums) + slot * ring_bytes<T, kC, kS>();
   uint64_t *bars = reinterpret_cast<uint64_t *>(ring);
   unsigned char *stages = ring + 128;
   const int c_lane = static_cast<int>(x0 - kC - ws) + kC * lane;
@@ -828,7 +829,6 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
   }
 
   if constexpr (kReduce) {
-    __shared__ double part[kWarps][3];
     double v0 = static_cast<double>(rs_num.x) + rs_num.y;
     double v1 = static_cast<double>(rs_den.x) + rs_den.y;
     double v2 = static_cast<double>(rs_mass.x) + rs_mass.y;
@@ -842,18 +842,11 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
                      !isfinite(v2);
     const bool any_bad = __any_sync(kFull, bad);
     if (lane == 0) {
-      part[warp][0] = v0;
-      part[warp][1] = v1;
-      part[warp][2] = v2;
+      double *q = a.partials + 3 * ((by * gx + bx) * kWarps + w);
+      q[0] = v0;
+      q[1] = v1;
+      q[2] = v2;
       if (any_bad) atomicOr(a.flag, kFlagUnstable);
-    }
-    __syncthreads();
-    if (threadIdx.x < 3) {
-      double s = 0.0;
-#pragma unroll
-      for (int w = 0; w < kWarps; ++w) s += part[w][threadIdx.x];
-      const int64_t b = by * gx + bx;
-      a.partials[3 * b + threadIdx.x] = s;
     }
   }
 }
@@ -865,32 +858,35 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks)
   SolidSums *lut = reinterpret_cast<SolidSums *>(smem);
   build_solid_lut(lut);
   __syncthreads();
-  step_tile<T, kC, kRows, kS, kReduce>(a, blockIdx.x, blockIdx.y, gridDim.x,
-                                       lut, smem);
+  const int warp = threadIdx.x / kLanes;
+  step_tile<T, kC, kRows, kS, kReduce>(a, blockIdx.x, blockIdx.y, warp, warp,
+                                       gridDim.x, lut, smem);
 }
 
-// Batched step: a persistent grid takes block tiles of many domains from one
-// work list through an atomic counter, so that one launch advances every
-// member of a batch by one step.  Tile for tile it runs the same code as the
-// single-domain kernel, so each member's result does not depend on the batch.
+// Batched step: a persistent grid whose warps take warp tiles of many domains
+// from one work list through an atomic counter, so that one launch advances
+// every member of a batch by one step.  Each warp works on its own (its own
+// ring, no block barrier between tiles), and tile for tile it runs the same
+// code as the single-domain kernel, so each member's result does not depend
+// on the batch.
 template <typename T, int kC, int kRows, int kMinBlocks, int kS, bool kReduce>
 __global__ void __launch_bounds__(kThreads, kMinBlocks)
     lbm_batch_kernel(const BatchLaunch b) {
   extern __shared__ __align__(128) unsigned char smem[];
   SolidSums *lut = reinterpret_cast<SolidSums *>(smem);
-  __shared__ int s_item;
   build_solid_lut(lut);
   // the batch clock: read by every block before the last block advances it
   const unsigned clock = *b.clock;
   __syncthreads();
   const int n = *b.nitems;
+  const int slot = threadIdx.x / kLanes;
   for (;;) {
-    if (threadIdx.x == 0) s_item = static_cast<int>(atomicAdd(b.counter, 1u));
-    __syncthreads();
-    const int it = s_item;
-    __syncthreads();
+    int it = 0;
+    if ((threadIdx.x & (kLanes - 1)) == 0)
+      it = static_cast<int>(atomicAdd(b.counter, 1u));
+    it = __shfl_sync(kFull, it, 0);
     if (it >= n) break;
-    const int4 w = b.items[it];  // member, tile x, tile y
+    const int4 w = b.items[it];  // member, tile x, tile y, warp
     const BatchMember &m = b.members[w.x];
     const int c = (m.cur ^ b.parity) & 1;
     StepLaunch a;
@@ -909,9 +905,12 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks)
     a.storage = b.storage;
     a.sr = m.sr;
     a.step = static_cast<uint32_t>(m.step_base) + clock;
-    step_tile<T, kC, kRows, kS, kReduce>(a, w.y, w.z, m.gx, lut, smem);
+    step_tile<T, kC, kRows, kS, kReduce>(a, w.y, w.z, w.w, slot, m.gx, lut,
+                                         smem);
   }
-  // the last block to finish advances the clock for the next launch
+  // the last block to finish advances the clock for the next launch (every
+  // thread read it before its block's first tile)
+  __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
     if (atomicAdd(b.done, 1u) == gridDim.x - 1) {
@@ -931,7 +930,16 @@ __global__ void batch_gather_kernel(const BatchMember *__restrict__ members,
     for (int q = 0; q < 4; ++q) out[4 * i + q] = members[i].result[q];
 }
 
-// One block per batch member: sums its block partials (fixed order) into its
+// The partial triple of block tile b: its warps' triples added in warp order.
+__device__ __forceinline__ double block_partial(const double *partials,
+                                               int64_t b, int q) {
+  double s = 0.0;
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w) s += partials[3 * (b * kWarps + w) + q];
+  return s;
+}
+
+// One block per batch member: sums its partials (fixed order) into its
 // result slot.
 __global__ void __launch_bounds__(256)
     batch_finalize_kernel(const BatchMember *__restrict__ members) {
@@ -939,7 +947,7 @@ __global__ void __launch_bounds__(256)
   const BatchMember &m = members[blockIdx.x];
   double s[3] = {0.0, 0.0, 0.0};
   for (int64_t k = threadIdx.x; k < m.nblocks; k += 256)
-    for (int q = 0; q < 3; ++q) s[q] += m.partials[3 * k + q];
+    for (int q = 0; q < 3; ++q) s[q] += block_partial(m.partials, k, q);
   for (int q = 0; q < 3; ++q) buf[q][threadIdx.x] = s[q];
   __syncthreads();
   for (int w = 128; w > 0; w >>= 1) {
@@ -958,7 +966,7 @@ __global__ void __launch_bounds__(kFinalizeThreads)
   __shared__ double buf[3][kFinalizeThreads];
   double s[3] = {0.0, 0.0, 0.0};
   for (int64_t b = threadIdx.x; b < nblocks; b += kFinalizeThreads)
-    for (int k = 0; k < 3; ++k) s[k] += partials[3 * b + k];
+    for (int k = 0; k < 3; ++k) s[k] += block_partial(partials, b, k);
   for (int k = 0; k < 3; ++k) buf[k][threadIdx.x] = s[k];
   __syncthreads();
   for (int w = kFinalizeThreads / 2; w > 0; w >>= 1) {

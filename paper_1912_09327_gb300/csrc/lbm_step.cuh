@@ -6,6 +6,10 @@
 
 namespace lbmtau1 {
 
+// Warps per block tile (stacked in y).  A reduced step writes one partial
+// triple per warp tile: kTileWarps triples per block tile.
+constexpr int kTileWarps = 4;
+
 // Storage formats (the LBM_STORAGE_* values of the C ABI).
 constexpr int kStorageF32 = 0;
 constexpr int kStorageF16 = 1;
@@ -27,7 +31,7 @@ struct StepLaunch {
   int64_t nx, ny, pitch;
   int periodic_x, periodic_y;
   float fx, fy;
-  double *partials;     // 3 doubles per block (reduced steps only)
+  double *partials;     // 3 doubles per warp tile (reduced steps only)
   unsigned int *flag;   // sticky instability flag (reduced steps only)
   int storage = kStorageF32;
   int variant = 0;      // tile variant (see choose_variant)
@@ -44,7 +48,7 @@ struct BatchMember {
   int64_t nx, ny, pitch;
   int periodic_x, periodic_y;
   float fx, fy;
-  double *partials;  // one triple per block tile
+  double *partials;  // one triple per warp tile
   double *result;    // 3 doubles, then the flag word
   unsigned int *flag;
   int64_t gx;        // block tiles along x for the batch's tile variant
@@ -56,7 +60,7 @@ struct BatchMember {
 
 struct BatchLaunch {
   const BatchMember *members;
-  const int4 *items;    // (member, tile x, tile y, 0)
+  const int4 *items;    // (member, tile x, tile y, warp): one per warp tile
   const int *nitems;
   unsigned int *counter;  // zeroed before the launch
   int parity;             // step index within the call, mod 2
@@ -97,7 +101,8 @@ int choose_variant(int64_t nx, int64_t ny, int storage);
 // (sum |du|^2, sum |u|^2, sum (rho - 1)) and raises the flag on instability.
 cudaError_t launch_step(const StepLaunch &a, bool reduce, cudaStream_t s);
 
-// Sums `nblocks` partial triples in FP64 in a fixed order into out[0..2].
+// Sums the partial triples of `nblocks` block tiles (kTileWarps each, added
+// in warp order per block) in FP64 in a fixed order into out[0..2].
 cudaError_t launch_finalize(const double *partials, int64_t nblocks,
                             double *out, cudaStream_t s);
 
