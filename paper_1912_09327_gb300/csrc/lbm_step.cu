@@ -958,15 +958,31 @@ __global__ void __launch_bounds__(256)
   if (threadIdx.x < 3) m.result[threadIdx.x] = buf[threadIdx.x][0];
 }
 
-constexpr int kFinalizeThreads = 512;
+constexpr int kFinalizeThreads = 1024;
 
 __global__ void __launch_bounds__(kFinalizeThreads)
     finalize_kernel(const double *__restrict__ partials, int64_t nblocks,
                     double *__restrict__ out) {
   __shared__ double buf[3][kFinalizeThreads];
   double s[3] = {0.0, 0.0, 0.0};
-  for (int64_t b = threadIdx.x; b < nblocks; b += kFinalizeThreads)
-    for (int k = 0; k < 3; ++k) s[k] += block_partial(partials, b, k);
+  for (int64_t b = threadIdx.x; b < nblocks; b += kFinalizeThreads) {
+    // the block tile's kWarps triples: 12 contiguous doubles, 16-byte aligned
+    const double2 *p = reinterpret_cast<const double2 *>(partials + 3 * kWarps * b);
+    double v[3 * kWarps];
+#pragma unroll
+    for (int i = 0; i < 3 * kWarps / 2; ++i) {
+      const double2 t = p[i];
+      v[2 * i] = t.x;
+      v[2 * i + 1] = t.y;
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      double t = 0.0;
+#pragma unroll
+      for (int w = 0; w < kWarps; ++w) t += v[3 * w + k];
+      s[k] += t;
+    }
+  }
   for (int k = 0; k < 3; ++k) buf[k][threadIdx.x] = s[k];
   __syncthreads();
   for (int w = kFinalizeThreads / 2; w > 0; w >>= 1) {
