@@ -90,7 +90,7 @@ typedef struct lbm_ctx lbm_ctx;
 /*
  * Device workspace needed for a domain, in bytes; 0 when p is invalid.
  * The workspace holds both copies of the three moment fields (rows padded to
- * a multiple of 32 nodes), the node-type array, per-block reduction partials
+ * a multiple of 32 nodes), the node-type array, per-warp-tile reduction partials
  * and a bounded staging buffer for host transfers.
  */
 size_t lbm_workspace_bytes(const lbm_params *p);

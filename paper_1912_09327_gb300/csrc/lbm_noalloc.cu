@@ -1,7 +1,7 @@
 // One LBMTau1 step with its residual reduction, on caller-owned device
 // fields, that allocates no memory at all.
 //
-// The regular entry points keep their reduction scratch (per-block partial
+// The regular entry points keep their reduction scratch (per-warp-tile partial
 // sums and the instability flag) in the device workspace that the caller
 // allocates for a context.  Some callers cannot allocate even that: a host
 // application that owns every byte of device memory through its own pool

@@ -38,11 +38,12 @@
 // every wait bounded in time), several rows ahead of use; at the domain's
 // edges the copies are clipped to the row and a periodic axis's wrapped
 // column arrives as one more 16-byte block.  On the last step of an lbm_step call the
-// same kernel reduces sum |du|^2, sum |u|^2 and sum delta (warp shuffles, FP64
-// block partials) and raises a sticky flag on rho <= 0 or non-finite values.
+// same kernel reduces sum |du|^2, sum |u|^2 and sum delta (warp shuffles, one
+// FP64 partial per warp tile) and raises a sticky flag on rho <= 0 or
+// non-finite values.
 // The storage type T (FP32, or FP16 / BF16 deviations) only changes loads and
 // stores; the arithmetic is FP32 throughout.  A batched kernel runs the same
-// tile code over a work list of many domains' tiles.
+// tile code, warp by warp, over a work list of many domains' warp tiles.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <float.h>
