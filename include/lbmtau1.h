@@ -132,7 +132,10 @@ int lbm_set_moments(lbm_ctx *ctx, const double *rho, const double *jx,
  * Enqueues nsteps LBMTau1 time steps (Algorithm 1), asynchronously.  The last
  * step of the call also reduces the residual and mass that lbm_residual
  * returns and checks for rho <= 0 or non-finite values.  nsteps = 0 is a
- * no-op.
+ * no-op.  On a stream that can be captured (not the legacy default stream,
+ * and not under a capture of the caller's), runs of 16 inner steps are
+ * replayed from a CUDA graph captured at first use (FP32 storage, or 16-bit
+ * storage rounded to nearest; stochastic rounding launches every step).
  * Errors: LBM_E_INVAL (nsteps < 0), LBM_E_STATE, LBM_E_CUDA (launch failure).
  */
 int lbm_step(lbm_ctx *ctx, int64_t nsteps);
@@ -238,7 +241,8 @@ int lbm_step_noalloc(const float *drho_in, const float *jx_in,
                      int32_t periodic_y, double fx, double fy,
                      double *dev_sums, uint32_t *dev_flags, void *cuda_stream);
 
-/* Frees the context's host state; the workspace stays the caller's. */
+/* Frees the context's host state and its captured step graphs; the
+ * workspace stays the caller's. */
 void lbm_destroy(lbm_ctx *ctx);
 
 /*

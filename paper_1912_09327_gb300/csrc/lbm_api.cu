@@ -155,6 +155,10 @@ int lbm_create(const lbm_params *p, void *dev_workspace, size_t workspace_bytes,
   c->cur = 0;
   c->variant = -1;
   c->steps = 0;
+  c->graph[0] = c->graph[1] = nullptr;
+  c->graph_variant[0] = c->graph_variant[1] = -1;
+  c->graphs_off = cuda_stream == nullptr || c->stream == cudaStreamLegacy ||
+                  c->stream == cudaStreamPerThread;
   c->has_geometry = false;
   c->has_residual = false;
   c->n_fluid = 0;
@@ -289,6 +293,66 @@ int lbm_get_state(lbm_ctx *c, void *drho, void *jx, void *jy) {
   return LBM_OK;
 }
 
+namespace {
+
+constexpr int64_t kGraphChunk = 16;  // steps per captured graph (even)
+
+// kGraphChunk unreduced steps from the current copy as one graph launch
+// (the copy holding the state is the same afterwards).  Falls back to direct
+// launches when the stream cannot be captured or is being captured already.
+int step_chunk(lbm_ctx *c, lbmtau1::StepLaunch a) {
+  const int p = c->cur;
+  auto direct = [&]() -> int {
+    for (int64_t t = 0; t < kGraphChunk; ++t) {
+      a.src = c->f[(p + t) & 1];
+      a.dst = c->f[(p + t + 1) & 1];
+      cudaError_t e = lbmtau1::launch_step(a, false, c->stream);
+      if (e != cudaSuccess) return cuda_fail(c, e, "step kernel launch");
+    }
+    return LBM_OK;
+  };
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (c->graphs_off || cudaStreamIsCapturing(c->stream, &cs) != cudaSuccess ||
+      cs != cudaStreamCaptureStatusNone) {
+    (void)cudaGetLastError();
+    return direct();
+  }
+  if (!c->graph[p] || c->graph_variant[p] != c->variant) {
+    if (c->graph[p]) cudaGraphExecDestroy(c->graph[p]);
+    c->graph[p] = nullptr;
+    if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) !=
+        cudaSuccess) {
+      (void)cudaGetLastError();
+      c->graphs_off = true;
+      return direct();
+    }
+    cudaError_t le = cudaSuccess;
+    for (int64_t t = 0; t < kGraphChunk && le == cudaSuccess; ++t) {
+      a.src = c->f[(p + t) & 1];
+      a.dst = c->f[(p + t + 1) & 1];
+      le = lbmtau1::launch_step(a, false, c->stream);
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    if (le != cudaSuccess || e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return cuda_fail(c, le != cudaSuccess ? le : e, "step graph capture");
+    }
+    e = cudaGraphInstantiate(&c->graph[p], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      c->graph[p] = nullptr;
+      return cuda_fail(c, e, "cudaGraphInstantiate");
+    }
+    c->graph_variant[p] = c->variant;
+  }
+  cudaError_t e = cudaGraphLaunch(c->graph[p], c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphLaunch");
+  return LBM_OK;
+}
+
+}  // namespace
+
 int lbm_step(lbm_ctx *c, int64_t nsteps) {
   if (!c) return LBM_E_INVAL;
   if (nsteps < 0) return fail(c, LBM_E_INVAL, "nsteps < 0");
@@ -312,13 +376,25 @@ int lbm_step(lbm_ctx *c, int64_t nsteps) {
   a.variant = c->variant;
   a.sr = c->p.storage != LBM_STORAGE_F32 &&
          c->p.rounding == LBM_ROUND_STOCHASTIC;
-  for (int64_t s = 0; s < nsteps; ++s) {
+  // Steps 1 .. nsteps - 2 go in captured graph chunks when the rounding
+  // draws no per-step random bits (the graph replays fixed launch arguments);
+  // the first step of each call (any one-time kernel set-up stays outside a
+  // capture) and the reduced last step are launched directly.
+  const bool graphs = !a.sr;
+  for (int64_t s = 0; s < nsteps;) {
+    if (graphs && s >= 1 && nsteps - 1 - s >= kGraphChunk) {
+      const int st = step_chunk(c, a);
+      if (st) return st;
+      s += kGraphChunk;
+      continue;
+    }
     a.src = c->f[c->cur];
     a.dst = c->f[1 - c->cur];
     a.step = static_cast<uint32_t>(c->steps + s);
     cudaError_t e = lbmtau1::launch_step(a, s == nsteps - 1, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "step kernel launch");
     c->cur = 1 - c->cur;
+    ++s;
   }
   cudaError_t e = lbmtau1::launch_finalize(
       c->partials, lbmtau1::launched_blocks(c->p.nx, c->p.ny, c->variant),
@@ -414,7 +490,12 @@ int lbm_residual(lbm_ctx *c, double *residual, double *mass) {
   return LBM_OK;
 }
 
-void lbm_destroy(lbm_ctx *c) { delete c; }
+void lbm_destroy(lbm_ctx *c) {
+  if (!c) return;
+  for (cudaGraphExec_t g : c->graph)
+    if (g) cudaGraphExecDestroy(g);
+  delete c;
+}
 
 const char *lbm_last_error(const lbm_ctx *c) {
   return c ? c->err : "null context";

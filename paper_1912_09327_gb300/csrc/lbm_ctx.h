@@ -38,6 +38,11 @@ struct lbm_ctx {
   int cur;              // copy holding the current state
   int variant;          // tile variant, chosen at the first step (-1 before)
   int64_t steps;        // steps taken (seeds stochastic rounding)
+  // 16 unreduced steps captured as one CUDA graph, one per starting copy
+  // (rebuilt when the tile variant changes); none on an uncapturable stream
+  cudaGraphExec_t graph[2];
+  int graph_variant[2];
+  bool graphs_off;
   bool has_geometry;
   bool has_residual;
   int64_t n_fluid;
