@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <new>
+#include <vector>
 
 #include "../../include/lbmtau1.h"
 #include "lbm_ctx.h"
@@ -56,6 +57,8 @@ Layout make_layout(const lbm_params *p) {
   off += align_up(static_cast<size_t>(L.nblocks) * lbmtau1::kTileWarps * 3 *
                       sizeof(double),
                   kAlign);
+  L.off_clean = off;
+  off += align_up(static_cast<size_t>(L.nblocks) * lbmtau1::kTileWarps, kAlign);
   L.off_result = off;
   off += kAlign;
   L.off_staging = off;
@@ -149,6 +152,8 @@ int lbm_create(const lbm_params *p, void *dev_workspace, size_t workspace_bytes,
   c->mask = reinterpret_cast<uint8_t *>(c->base + L.off_mask);
   c->partials = reinterpret_cast<double *>(c->base + L.off_partials);
   c->result = reinterpret_cast<double *>(c->base + L.off_result);
+  c->clean = reinterpret_cast<uint8_t *>(c->base + L.off_clean);
+  c->clean_variant = -1;
   c->flag = reinterpret_cast<unsigned *>(c->result + 3);
   c->staging = reinterpret_cast<double *>(c->base + L.off_staging);
   c->stream = static_cast<cudaStream_t>(cuda_stream);
@@ -201,6 +206,7 @@ int lbm_set_geometry(lbm_ctx *c, const uint8_t *host_mask) {
   if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamSynchronize");
   c->cur = 0;
   c->n_fluid = fluid;
+  c->clean_variant = -1;  // new node types: flags computed again
   c->has_geometry = true;
   c->err[0] = '\0';
   return LBM_OK;
@@ -295,6 +301,35 @@ int lbm_get_state(lbm_ctx *c, void *drho, void *jx, void *jy) {
 
 namespace {
 
+// Picks the context's tile variant (first step): the model's choice, or its
+// twin with the clean-tile code when the grid is large and at least 3/4 of
+// the warp tiles are clean (the flags are read to the host once).
+int select_variant(lbm_ctx *c) {
+  int v = lbmtau1::choose_variant(c->p.nx, c->p.ny, c->p.storage);
+  const int d = lbmtau1::dual_variant(v, c->p.nx, c->p.ny);
+  if (d >= 0) {
+    // the dual kernel when at least 3/4 of the warp tiles are clean (its
+    // flags are v's: same tiles); one read of the flags to the host
+    cudaError_t e = lbmtau1::launch_tile_flags(d, c->mask, c->p.nx, c->p.ny,
+                                               c->L.pitch, c->clean,
+                                               c->stream);
+    const int64_t n = lbmtau1::launched_blocks(c->p.nx, c->p.ny, d) *
+                      lbmtau1::kTileWarps;
+    std::vector<uint8_t> h(static_cast<size_t>(n));
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(h.data(), c->clean, h.size(),
+                          cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "tile flags");
+    int64_t clean = 0;
+    for (uint8_t f : h) clean += f;
+    if (4 * clean >= 3 * n) v = d;
+    c->clean_variant = v;  // same tiles either way
+  }
+  c->variant = v;
+  return LBM_OK;
+}
+
 constexpr int64_t kGraphChunk = 16;  // steps per captured graph (even)
 
 // kGraphChunk unreduced steps from the current copy as one graph launch
@@ -371,9 +406,19 @@ int lbm_step(lbm_ctx *c, int64_t nsteps) {
   a.partials = c->partials;
   a.flag = c->flag;
   a.storage = c->p.storage;
-  if (c->variant < 0)
-    c->variant = lbmtau1::choose_variant(c->p.nx, c->p.ny, c->p.storage);
+  if (c->variant < 0) {
+    const int st = select_variant(c);
+    if (st) return st;
+  }
   a.variant = c->variant;
+  if (c->clean_variant != c->variant) {
+    cudaError_t e = lbmtau1::launch_tile_flags(c->variant, c->mask, c->p.nx,
+                                               c->p.ny, c->L.pitch, c->clean,
+                                               c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "tile flags kernel launch");
+    c->clean_variant = c->variant;
+  }
+  a.clean = c->clean;
   a.sr = c->p.storage != LBM_STORAGE_F32 &&
          c->p.rounding == LBM_ROUND_STOCHASTIC;
   // Steps 1 .. nsteps - 2 go in captured graph chunks when the rounding
@@ -428,8 +473,12 @@ int lbm_set_variant(lbm_ctx *c, int32_t variant) {
 
 int32_t lbm_variant(lbm_ctx *c) {
   if (!c) return -1;
-  if (c->variant < 0)
-    c->variant = lbmtau1::choose_variant(c->p.nx, c->p.ny, c->p.storage);
+  if (c->variant < 0) {
+    // before the node types are known only the model's choice (not kept)
+    if (!c->has_geometry)
+      return lbmtau1::choose_variant(c->p.nx, c->p.ny, c->p.storage);
+    if (select_variant(c) != LBM_OK) return -1;
+  }
   return c->variant;
 }
 

@@ -118,7 +118,7 @@ int upload(lbm_batch *b) {
   lbmtau1::variant_tile(b->variant, &tx, &ty);
   b->h_members.resize(n);
   for (int i = 0; i < n; ++i) {
-    const lbm_ctx *c = b->packed[i];
+    lbm_ctx *c = b->packed[i];
     BatchMember &m = b->h_members[i];
     m.f[0] = c->f[0];
     m.f[1] = c->f[1];
@@ -139,6 +139,14 @@ int upload(lbm_batch *b) {
     m.sr = c->p.storage != LBM_STORAGE_F32 &&
            c->p.rounding == LBM_ROUND_STOCHASTIC;
     m.step_base = c->steps - static_cast<int64_t>(b->clock);
+    if (c->clean_variant != b->variant) {  // clean-tile flags for our tiles
+      cudaError_t e = lbmtau1::launch_tile_flags(
+          b->variant, c->mask, c->p.nx, c->p.ny, c->L.pitch, c->clean,
+          b->stream);
+      if (e != cudaSuccess) return bcuda(b, e, "tile flags kernel launch");
+      c->clean_variant = b->variant;
+    }
+    m.clean = c->clean;
   }
   if (b->items_dirty) {
     b->h_items.clear();

@@ -17,6 +17,7 @@ struct Layout {
   size_t off_fields = 0;    // 6 planes: copy 0 (d, jx, jy), copy 1 (d, jx, jy)
   size_t off_mask = 0;
   size_t off_partials = 0;
+  size_t off_clean = 0;     // one byte per warp tile: clean-tile flags
   size_t off_result = 0;    // 3 doubles + flag
   size_t off_staging = 0;
   size_t total = 0;
@@ -31,6 +32,8 @@ struct lbm_ctx {
   lbmtau1::Fields f[2];
   uint8_t *mask;
   double *partials;
+  uint8_t *clean;       // clean-tile flags of tile variant clean_variant
+  int clean_variant;    // -1: not computed for the current node types
   double *result;       // sum |du|^2, sum |u|^2, sum (rho - 1)
   unsigned *flag;       // follows the three doubles
   double *staging;

@@ -373,8 +373,11 @@ __host__ __device__ constexpr int smem_bytes() {
 // tile (bx, by), (30 kC) columns x kRows rows.  `gx` is the number of block
 // tiles along x (for the index of the warp's reduction partial); `slot` is
 // the calling warp's place in its block, which owns a shared-memory ring.
-// Every lane of the warp calls it; no other warp takes part.
-template <typename T, int kC, int kRows, int kS, bool kReduce>
+// Every lane of the warp calls it; no other warp takes part.  kClean: the
+// warp tile's marched rows and columns all lie inside the domain and hold
+// fluid nodes only (see tile_flags_kernel), so node types, edges and wall
+// terms need no handling and the node-type rows are not copied.
+template <typename T, int kC, int kRows, int kS, bool kReduce, bool kClean>
 __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
                                           int64_t by, int w, int slot,
                                           int64_t gx, const SolidSums *lut,
@@ -473,14 +476,15 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
       unsigned char *dmask = dst + 3 * St::kFieldBytes;
       if (interior) {  // the whole window lies in the row
         const int64_t off = static_cast<int64_t>(r) * a.pitch + ws;
-        mbar_expect_tx(bar, 3 * St::kFieldBytes + St::kMaskBytes);
+        mbar_expect_tx(bar, 3 * St::kFieldBytes + (kClean ? 0 : St::kMaskBytes));
         bulk_copy(dst, static_cast<const T *>(a.src.d) + off, St::kFieldBytes,
                   bar);
         bulk_copy(dst + St::kFieldBytes,
                   static_cast<const T *>(a.src.jx) + off, St::kFieldBytes, bar);
         bulk_copy(dst + 2 * St::kFieldBytes,
                   static_cast<const T *>(a.src.jy) + off, St::kFieldBytes, bar);
-        bulk_copy(dmask, a.mask + r * a.pitch + m0, St::kMaskBytes, bar);
+        if (!kClean)
+          bulk_copy(dmask, a.mask + r * a.pitch + m0, St::kMaskBytes, bar);
         return;
       }
       constexpr int64_t kA = St::kAlignElems;
@@ -489,7 +493,7 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
       const int64_t k0 = max(m0, int64_t(0));
       const int64_t k1 = min(m0 + St::kMaskBytes, (a.nx + 15) & ~int64_t(15));
       const uint32_t fbytes = static_cast<uint32_t>((c1 - c0) * sizeof(T));
-      const uint32_t mbytes = static_cast<uint32_t>(k1 - k0);
+      const uint32_t mbytes = kClean ? 0u : static_cast<uint32_t>(k1 - k0);
       mbar_expect_tx(bar, 3 * fbytes + mbytes + (wrap_l ? 64u : 0u) +
                               (wrap_r ? 64u : 0u));
       const int64_t rp = static_cast<int64_t>(r) * a.pitch;
@@ -501,7 +505,7 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
 #pragma unroll
       for (int f = 0; f < 3; ++f)
         bulk_copy(dst + f * St::kFieldBytes + foff, src[f] + c0, fbytes, bar);
-      bulk_copy(dmask + (k0 - m0), mrow + k0, mbytes, bar);
+      if (!kClean) bulk_copy(dmask + (k0 - m0), mrow + k0, mbytes, bar);
       if (wrap_l) {  // the blocks holding column nx - 1, into the window head
         const int64_t lf = (a.nx - 1) & ~(kA - 1), lm = (a.nx - 1) & ~int64_t(15);
 #pragma unroll
@@ -518,6 +522,23 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
     };
     // ring row i -> registers; false when the copy did not arrive in time
     auto fetch = [&](int i, RawRow<kC> &o) -> bool {
+      if constexpr (kClean) {  // an in-domain row of fluid nodes
+        const unsigned ui = static_cast<unsigned>(i);
+        const int st = static_cast<int>(ui % kS);
+        const bool ok = mbar_wait(bars + st, (ui / kS) & 1u);
+        const unsigned char *src = stages + st * St::kBytes;
+        load_vec<kC, T>(reinterpret_cast<const T *>(src) + c_lane, o.d,
+                        1.0f / SS::kD, false);
+        load_vec<kC, T>(reinterpret_cast<const T *>(src + St::kFieldBytes) +
+                            c_lane,
+                        o.jx, 1.0f / SS::kJ, false);
+        load_vec<kC, T>(reinterpret_cast<const T *>(src + 2 * St::kFieldBytes) +
+                            c_lane,
+                        o.jy, 1.0f / SS::kJ, false);
+        o.solid = 0u;
+        o.fluid = (1u << kC) - 1u;
+        return ok;
+      }
       if (source_row(i) < 0) {
 #pragma unroll
         for (int j = 0; j < kC; ++j) o.d[j] = o.jx[j] = o.jy[j] = 0.f;
@@ -642,14 +663,18 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
       LBM_HALO(G)
       LBM_HALO(X)
 #undef LBM_HALO
-      const unsigned sbits = ra.solid | (rb.solid << kC);
-      const unsigned sl = __shfl_up_sync(kFull, sbits, 1);
-      const unsigned sr = __shfl_down_sync(kFull, sbits, 1);
-      const unsigned A6 = ((sl >> (kC - 1)) & 1u) | (ra.solid << 1) |
-                          ((sr & 1u) << (kC + 1));
-      const unsigned B6 = ((sl >> (2 * kC - 1)) & 1u) | (rb.solid << 1) |
-                          (((sr >> kC) & 1u) << (kC + 1));
-      const bool any_solid = __any_sync(kFull, (pA6 | pB6 | A6 | B6) != 0u);
+      unsigned A6 = 0u, B6 = 0u;
+      bool any_solid = false;
+      if constexpr (!kClean) {
+        const unsigned sbits = ra.solid | (rb.solid << kC);
+        const unsigned sl = __shfl_up_sync(kFull, sbits, 1);
+        const unsigned sr = __shfl_down_sync(kFull, sbits, 1);
+        A6 = ((sl >> (kC - 1)) & 1u) | (ra.solid << 1) |
+             ((sr & 1u) << (kC + 1));
+        B6 = ((sl >> (2 * kC - 1)) & 1u) | (rb.solid << 1) |
+             (((sr >> kC) & 1u) << (kC + 1));
+        any_solid = __any_sync(kFull, (pA6 | pB6 | A6 | B6) != 0u);
+      }
 
       float od0[kC], ox0[kC], oy0[kC], od1[kC], ox1[kC], oy1[kC];
 #pragma unroll
@@ -696,7 +721,7 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
                            add(acc_mx, F2x));
         float2 incy = fma2(half, add(sub(zpy[j], jyO), sub(zy[C], jyO)),
                            add(acc_my, F2y));
-        if (any_solid) {
+        if (!kClean && any_solid) {
           const unsigned c0 = ((pA6 >> j) & 7u) | (((pB6 >> j) & 7u) << 3) |
                               (((A6 >> j) & 7u) << 6);
           const unsigned c1 = ((pB6 >> j) & 7u) | (((A6 >> j) & 7u) << 3) |
@@ -708,7 +733,8 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
         }
         const float2 mxn = add(jxO, incx);
         const float2 myn = add(jyO, incy);
-        const bool f0 = (pfluidB >> j) & 1u, f1 = (ra.fluid >> j) & 1u;
+        const bool f0 = kClean || ((pfluidB >> j) & 1u);
+        const bool f1 = kClean || ((ra.fluid >> j) & 1u);
         od0[j] = f0 ? dn.x : dO.x;
         ox0[j] = f0 ? mxn.x : jxO.x;
         oy0[j] = f0 ? myn.x : jyO.x;
@@ -852,7 +878,30 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
   }
 }
 
-template <typename T, int kC, int kRows, int kMinBlocks, int kS, bool kReduce>
+// Runs warp tile (bx, by, w).  kDual: with the code for clean tiles when
+// the tile's flag says so (flags absent: the general code); otherwise the
+// general code only, which keeps the kernel's registers for one code path.
+template <typename T, int kC, int kRows, int kS, bool kReduce, bool kDual>
+__device__ __forceinline__ void run_tile(const StepLaunch &a, int64_t bx,
+                                         int64_t by, int w, int slot,
+                                         int64_t gx, const SolidSums *lut,
+                                         unsigned char *smem) {
+  if constexpr (!kDual) {
+    step_tile<T, kC, kRows, kS, kReduce, false>(a, bx, by, w, slot, gx, lut,
+                                                smem);
+    return;
+  }
+  const bool clean = a.clean && a.clean[(by * gx + bx) * kWarps + w];
+  if (clean)
+    step_tile<T, kC, kRows, kS, kReduce, true>(a, bx, by, w, slot, gx, lut,
+                                               smem);
+  else
+    step_tile<T, kC, kRows, kS, kReduce, false>(a, bx, by, w, slot, gx, lut,
+                                                smem);
+}
+
+template <typename T, int kC, int kRows, int kMinBlocks, int kS, bool kReduce,
+          bool kDual>
 __global__ void __launch_bounds__(kThreads, kMinBlocks)
     lbm_step_kernel(const StepLaunch a) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -860,8 +909,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks)
   build_solid_lut(lut);
   __syncthreads();
   const int warp = threadIdx.x / kLanes;
-  step_tile<T, kC, kRows, kS, kReduce>(a, blockIdx.x, blockIdx.y, warp, warp,
-                                       gridDim.x, lut, smem);
+  run_tile<T, kC, kRows, kS, kReduce, kDual>(a, blockIdx.x, blockIdx.y, warp,
+                                             warp, gridDim.x, lut, smem);
 }
 
 // Batched step: a persistent grid whose warps take warp tiles of many domains
@@ -870,7 +919,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks)
 // ring, no block barrier between tiles), and tile for tile it runs the same
 // code as the single-domain kernel, so each member's result does not depend
 // on the batch.
-template <typename T, int kC, int kRows, int kMinBlocks, int kS, bool kReduce>
+template <typename T, int kC, int kRows, int kMinBlocks, int kS, bool kReduce,
+          bool kDual>
 __global__ void __launch_bounds__(kThreads, kMinBlocks)
     lbm_batch_kernel(const BatchLaunch b) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -906,8 +956,9 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks)
     a.storage = b.storage;
     a.sr = m.sr;
     a.step = static_cast<uint32_t>(m.step_base) + clock;
-    step_tile<T, kC, kRows, kS, kReduce>(a, w.y, w.z, w.w, slot, m.gx, lut,
-                                         smem);
+    a.clean = m.clean;
+    run_tile<T, kC, kRows, kS, kReduce, kDual>(a, w.y, w.z, w.w, slot, m.gx,
+                                               lut, smem);
   }
   // the last block to finish advances the clock for the next launch (every
   // thread read it before its block's first tile)
@@ -920,6 +971,37 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks)
       __threadfence();
     }
   }
+}
+
+// One warp per warp tile: 1 when the tile is clean (see launch_tile_flags).
+template <int kC, int kRows>
+__global__ void tile_flags_kernel(const uint8_t *__restrict__ mask,
+                                  int64_t nx, int64_t ny, int64_t pitch,
+                                  int64_t gx, int64_t ntiles,
+                                  uint8_t *__restrict__ out) {
+  constexpr int kTile = (kLanes - 2) * kC;
+  const int64_t t = (static_cast<int64_t>(blockIdx.x) * blockDim.x +
+                     threadIdx.x) / kLanes;
+  const int lane = threadIdx.x & (kLanes - 1);
+  if (t >= ntiles) return;  // whole warps leave together
+  const int64_t block = t / kWarps, w = t % kWarps;
+  const int64_t x0 = (block % gx) * kTile, y0 = (block / gx * kWarps + w) * kRows;
+  // rows y0 - 1 .. y0 + kRows and columns x0 - kC .. x0 + 31 kC - 1
+  bool ok = x0 - kC >= 0 && x0 + (kLanes - 1) * kC <= nx && y0 >= 1 &&
+            y0 + kRows <= ny - 1;
+  if (ok) {
+    const int64_t xb = x0 - kC + static_cast<int64_t>(kC) * lane;
+    for (int64_t y = y0 - 1; y <= y0 + kRows && ok; ++y) {
+      const uint8_t *p = mask + y * pitch + xb;
+      unsigned m;
+      if constexpr (kC == 4)
+        m = *reinterpret_cast<const unsigned *>(p);
+      else
+        m = *reinterpret_cast<const unsigned short *>(p);
+      ok = __all_sync(kFull, m == 0u);
+    }
+  }
+  if (lane == 0) out[t] = ok ? 1 : 0;
 }
 
 // Copies every member's result slot (3 sums and the flag word) into out,
@@ -1052,9 +1134,12 @@ __global__ void solid_storage_kernel(Fields f, const uint8_t *__restrict__ mask,
 // SM requested from the register allocator, shared-memory ring stages.
 struct Variant {
   int cols, rows, min_blocks, stages;
+  bool dual;  // also carries the clean-tile code (flags per warp tile)
 };
-constexpr Variant kVariants[] = {{4, 64, 2, 8},  {2, 64, 3, 12}, {4, 32, 2, 8},
-                                  {2, 64, 4, 10}, {4, 8, 2, 8},   {2, 8, 3, 12}};
+constexpr Variant kVariants[] = {
+    {4, 64, 2, 8, false}, {2, 64, 3, 12, false}, {4, 32, 2, 8, false},
+    {2, 64, 4, 10, false}, {4, 8, 2, 8, false},  {2, 8, 3, 12, false},
+    {4, 64, 2, 8, true}};
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
 // Calls f(std::integral_constant<int, v>) for a run-time variant index v
@@ -1100,7 +1185,7 @@ cudaError_t launch_variant(const StepLaunch &a, dim3 g, cudaStream_t s) {
   constexpr int smem = smem_bytes<T, v.cols, v.stages>();
   static_assert(smem <= 227 * 1024, "shared memory per block");
   auto kern =
-      lbm_step_kernel<T, v.cols, v.rows, v.min_blocks, v.stages, kReduce>;
+      lbm_step_kernel<T, v.cols, v.rows, v.min_blocks, v.stages, kReduce, v.dual>;
   static cudaError_t attr = cudaFuncSetAttribute(
       kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (attr != cudaSuccess) return attr;
@@ -1121,7 +1206,8 @@ template <typename T, int kV>
 int occupancy_of() {
   constexpr Variant v = kVariants[kV];
   constexpr int smem = smem_bytes<T, v.cols, v.stages>();
-  auto kern = lbm_step_kernel<T, v.cols, v.rows, v.min_blocks, v.stages, false>;
+  auto kern =
+      lbm_step_kernel<T, v.cols, v.rows, v.min_blocks, v.stages, false, v.dual>;
   static int occ = [&] {
     int n = 0;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1175,6 +1261,7 @@ int choose_variant_t(int64_t nx, int64_t ny) {
     const double block_time =
         (v.rows + 2.0) * v.cols * (v.cols == 2 ? kTwoColumnCost : 1.0);
     const double rate = (occ >= 2 && per_sm >= 2) ? kSharedSpeedup : 1.0;
+    if (v.dual) continue;  // chosen only through dual_variant, by its flags
     const double t = static_cast<double>(per_sm) * block_time / rate;
     if (best_time == 0.0 || t < best_time * (1.0 - 1e-9)) {
       best_time = t;
@@ -1189,7 +1276,8 @@ cudaError_t launch_batch_variant(const BatchLaunch &b, cudaStream_t s) {
   constexpr Variant v = kVariants[kV];
   constexpr int smem = smem_bytes<T, v.cols, v.stages>();
   auto kern =
-      lbm_batch_kernel<T, v.cols, v.rows, v.min_blocks, v.stages, kReduce>;
+      lbm_batch_kernel<T, v.cols, v.rows, v.min_blocks, v.stages, kReduce,
+                       v.dual>;
   // persistent grid: every resident block slot of the device, computed once
   static int grid = [&] {
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1287,6 +1375,33 @@ int64_t launched_blocks(int64_t nx, int64_t ny, int variant) {
   return static_cast<int64_t>(g.x) * g.y;
 }
 
+int dual_variant(int v, int64_t nx, int64_t ny) {
+  if (forced_variant() >= 0 || v < 0 || v >= kNumVariants) return -1;
+  const Variant b = kVariants[v];
+  if (b.dual) return -1;
+  static int sms = [] {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) !=
+            cudaSuccess)
+      n = 0;
+    return n;
+  }();
+  // the clean-tile code pays off only over many waves of blocks (measured:
+  // +2 to +14 % from 8192^2 up, a few per cent slower at 4096^2 and below,
+  // where the edge tiles' general code, which the dual kernel runs with
+  // fewer free registers, sets the step time)
+  if (sms <= 0 || launched_blocks(nx, ny, v) < 8 * static_cast<int64_t>(sms))
+    return -1;
+  for (int i = 0; i < kNumVariants; ++i) {
+    const Variant d = kVariants[i];
+    if (d.dual && d.cols == b.cols && d.rows == b.rows &&
+        d.min_blocks == b.min_blocks && d.stages == b.stages)
+      return i;
+  }
+  return -1;
+}
+
 int choose_variant(int64_t nx, int64_t ny, int storage) {
   const int f = forced_variant();
   if (f >= 0) return f;
@@ -1305,6 +1420,24 @@ cudaError_t launch_step(const StepLaunch &a, bool reduce, cudaStream_t s) {
     case kStorageBF16: return launch_step_t<__nv_bfloat16>(a, reduce, s);
     default: return launch_step_t<float>(a, reduce, s);
   }
+}
+
+cudaError_t launch_tile_flags(int v, const uint8_t *mask, int64_t nx,
+                              int64_t ny, int64_t pitch, uint8_t *out,
+                              cudaStream_t s) {
+  if (v < 0 || v >= kNumVariants) return cudaErrorInvalidValue;
+  const dim3 g = step_grid(nx, ny, v);
+  const int64_t ntiles = static_cast<int64_t>(g.x) * g.y * kWarps;
+  const int64_t blocks = (ntiles * kLanes + 255) / 256;
+  (void)cudaGetLastError();
+  with_variant(v, [&](auto kv) {
+    constexpr Variant t = kVariants[decltype(kv)::value];
+    tile_flags_kernel<t.cols, t.rows><<<static_cast<unsigned>(blocks), 256, 0,
+                                        s>>>(mask, nx, ny, pitch, g.x, ntiles,
+                                             out);
+    return 0;
+  });
+  return cudaGetLastError();
 }
 
 cudaError_t launch_finalize(const double *partials, int64_t nblocks,

@@ -37,6 +37,9 @@ struct StepLaunch {
   int variant = 0;      // tile variant (see choose_variant)
   int sr = 0;           // 16-bit storage: stochastic rounding
   uint32_t step = 0;    // the domain's step count (seeds the rounding)
+  // one byte per warp tile of this launch's tile variant: 1 when the tile
+  // is clean (launch_tile_flags); null: every tile takes the general code
+  const uint8_t *clean = nullptr;
 };
 
 // One member of a batch (see launch_batch): both field copies, the copy that
@@ -56,6 +59,7 @@ struct BatchMember {
   int cur;           // copy holding the state when the batch step starts
   int sr;            // 16-bit storage: stochastic rounding
   int64_t step_base; // member's step count minus the batch clock
+  const uint8_t *clean;  // clean-tile flags for the batch's variant
 };
 
 struct BatchLaunch {
@@ -96,6 +100,22 @@ int64_t launched_blocks(int64_t nx, int64_t ny, int variant);
 // fills the device (queries the current device once).  All variants give
 // bit-identical results.
 int choose_variant(int64_t nx, int64_t ny, int storage);
+
+// The variant with v's tiles and, in the same kernel, the code for clean
+// tiles (see launch_tile_flags), when v's grid for an nx x ny domain is large
+// enough for it to pay off and no variant is forced; else -1.  The caller
+// takes it when most warp tiles are clean.
+int dual_variant(int v, int64_t nx, int64_t ny);
+
+// Writes one byte per warp tile of tile variant v for an nx x ny domain
+// (block tiles in row-major order, kTileWarps per block tile): 1 when every
+// row and column the warp tile marches (its rows plus one above and below,
+// its lanes' columns including the halo lanes) lies inside the domain and
+// holds a fluid node (type 0).  out holds launched_blocks(nx, ny, v) *
+// kTileWarps bytes.
+cudaError_t launch_tile_flags(int v, const uint8_t *mask, int64_t nx,
+                              int64_t ny, int64_t pitch, uint8_t *out,
+                              cudaStream_t s);
 
 // Enqueues one step; `reduce` also writes block partials of
 // (sum |du|^2, sum |u|^2, sum (rho - 1)) and raises the flag on instability.

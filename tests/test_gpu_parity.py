@@ -158,6 +158,34 @@ def test_domain_edges_every_variant(binding, storage):
                                              else np.uint32)), (nx, per)
 
 
+def test_clean_tile_kernel_on_large_domains(binding):
+    """A domain large enough (here 8192^2: 2208 block tiles of the tall
+    variant) whose warp tiles are mostly clean (interior, fluid only) gets
+    the variant whose kernel also carries the code for clean tiles; it gives
+    the state and the residual of the general kernel on the same tiles, bit
+    for bit."""
+    nx, ny = 8192, 8192
+    p = wl.random_problem(nx, ny, seed=77, amp=0.02, p_solid=0.0, p_fixed=0.0,
+                          periodic=(True, True), force=(1e-4, -5e-5))
+    p.mask[1000:1010, 3000:3050] = wl.SOLID   # a few tiles with walls
+    p.mask[4000, 100:140] = wl.FIXED
+    d = binding.Domain.from_problem(p)
+    v = d.variant()
+    tx, ty, cols = binding.lbm_variant_tile(v)
+    assert v != 0 and (tx, ty) == binding.lbm_variant_tile(0)[:2]
+    d.step(6)
+    got = d.get_state(), d.residual()
+    d.close()
+    d = binding.Domain.from_problem(p)
+    d.set_variant(0)
+    d.step(6)
+    want = d.get_state(), d.residual()
+    d.close()
+    for a, b in zip(got[0], want[0]):
+        assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
+    assert got[1] == want[1]
+
+
 def test_graph_chunks_equal_direct_launches(binding):
     """On a capturable stream lbm_step replays runs of 16 inner steps from a
     captured CUDA graph; on the default stream it launches every step.  Both
