@@ -677,6 +677,7 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
       }
 
       float od0[kC], ox0[kC], oy0[kC], od1[kC], ox1[kC], oy1[kC];
+      const bool acc_pair = owner && k > 0;  // clean tiles: outputs to sum
 #pragma unroll
       for (int j = 0; j < kC; ++j) {
         const int L = j, C = j + 1, R = j + 2;
@@ -757,17 +758,32 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
           const float2 ey = fma2(mul(jyO, iro), mdd, sub(myn, jyO));
           const float2 nn = mul(fma2(ex, ex, mul(ey, ey)), irn2);
           const float2 dd2 = mul(fma2(mxn, mxn, mul(myn, myn)), irn2);
-          if (v0) {
-            rs_num.x += nn.x;
-            rs_den.x += dd2.x;
-            rs_mass.x += dn.x;
-            rmin = fminf(rmin, rn.x);
-          }
-          if (v1) {
-            rs_num.y += nn.y;
-            rs_den.y += dd2.y;
-            rs_mass.y += dn.y;
-            rmin = fminf(rmin, rn.y);
+          if constexpr (kClean) {
+            // a clean tile is full height with every column in the domain:
+            // both rows count exactly when the pair has outputs.  The packed
+            // sums add the same non-negative terms in the same order as the
+            // scalar ones below; the compiler may fuse a packed scale and add
+            // (one rounding instead of two), so the two agree to float
+            // rounding
+            if (acc_pair) {
+              rs_num = add(rs_num, nn);
+              rs_den = add(rs_den, dd2);
+              rs_mass = add(rs_mass, dn);
+              rmin = fminf(rmin, fminf(rn.x, rn.y));
+            }
+          } else {
+            if (v0) {
+              rs_num.x += nn.x;
+              rs_den.x += dd2.x;
+              rs_mass.x += dn.x;
+              rmin = fminf(rmin, rn.x);
+            }
+            if (v1) {
+              rs_num.y += nn.y;
+              rs_den.y += dd2.y;
+              rs_mass.y += dn.y;
+              rmin = fminf(rmin, rn.y);
+            }
           }
         }
         // carry to the next pair
