@@ -63,15 +63,28 @@ extern "C" {
                               (12 B/node, 2 copies) */
 #define LBM_STORAGE_BF16 2 /* as bfloat16, unscaled (12 B/node, 2 copies) */
 
-/* Rounding of the 16-bit storage formats (FP32 storage ignores it).
- * Stochastic rounding rounds each stored value up or down with probabilities
- * that make its expected value exact, drawing the random bits from a counter-
- * based hash of (column, row, field, step count): a run is reproducible bit
- * for bit, and increments smaller than half a unit in the last place are not
- * lost (under round-to-nearest a slowly converging flow stalls far from its
- * steady state).  It is the default. */
-#define LBM_ROUND_STOCHASTIC 0
+/* Rounding of the stored moments.
+ * Stochastic rounding rounds a stored value up or down with probabilities
+ * that make its expected value exact: increments smaller than half a unit in
+ * the last place are not lost, and a near-constant increment (a body force
+ * accelerating a flow) does not round the same way step after step.  Under
+ * round-to-nearest a slowly converging flow stalls far from its steady state
+ * in the 16-bit formats, and in FP32 a uniformly accelerated flow drifts by
+ * up to half a unit in the last place per step (2e-5 relative after 2000
+ * steps of the 754 x 246 channel of the batched mix, where stochastic
+ * rounding keeps it at 3e-7).  Its price is noise: a steady state keeps
+ * jittering by about one unit in the last place per step, which bounds the
+ * residual a solve can reach from below.
+ *   - 16-bit formats: every stored value, with random bits from a counter-
+ *     based hash of (column, row, field, step count).
+ *   - FP32: the momentum (rho - 1 rounds to nearest), by adding to each
+ *     momentum increment a dither uniform over one unit in the last place of
+ *     the stored value, drawn once per step from the step count.
+ * Both are reproducible bit for bit.  The default is stochastic rounding
+ * for the 16-bit formats and rounding to nearest for FP32. */
+#define LBM_ROUND_DEFAULT 0
 #define LBM_ROUND_NEAREST 1
+#define LBM_ROUND_STOCHASTIC 2
 
 /* Problem statement.  Zero-initialise before filling in. */
 typedef struct lbm_params {
@@ -82,21 +95,27 @@ typedef struct lbm_params {
   double fx;          /* body force, momentum added per node per step */
   double fy;
   int32_t storage;    /* LBM_STORAGE_F32, _F16 or _BF16 */
-  int32_t rounding;   /* LBM_ROUND_STOCHASTIC (0) or LBM_ROUND_NEAREST */
+  int32_t rounding;   /* LBM_ROUND_DEFAULT (0), _NEAREST or _STOCHASTIC */
 } lbm_params;
 
 typedef struct lbm_ctx lbm_ctx;
 
 /*
  * Device workspace needed for a domain, in bytes; 0 when p is invalid.
- * The workspace holds both copies of the three moment fields (rows padded to
- * a multiple of 32 nodes), the node-type array, per-warp-tile reduction partials
- * and a bounded staging buffer for host transfers.
+ * The storage model is the paper's, Eq. (LBMTau1memory) in Section 5: two
+ * copies of N_f = 3 moment fields per node, 2 N_f c bytes (24 B in FP32,
+ * against (2Q + N_f) c = 84 B for standard D2Q9, Eq. (lbmmemory)).  The
+ * workspace holds both copies of the three moment fields (rows padded to a
+ * multiple of 32 nodes), the node-type array (the flag array F of
+ * Algorithm 1, 1 B per node), per-warp-tile reduction partials and a
+ * bounded staging buffer for host transfers.
  */
 size_t lbm_workspace_bytes(const lbm_params *p);
 
 /*
- * Creates a context over a caller-owned device workspace.
+ * Creates a context over a caller-owned device workspace: the two grids
+ * R_c, U_c, V_c (c = 0, 1) of Algorithm 1 and the flag array F, laid out as
+ * lbm_workspace_bytes describes.
  *   p               problem statement (copied).
  *   dev_workspace   device pointer, 256-byte aligned, >= lbm_workspace_bytes(p)
  *                   bytes; owned by the caller and must outlive the context.
@@ -153,6 +172,20 @@ int lbm_step(lbm_ctx *ctx, int64_t nsteps);
  */
 int lbm_set_variant(lbm_ctx *ctx, int32_t variant);
 int32_t lbm_variant(lbm_ctx *ctx);
+
+/*
+ * Failure detection (Section 5 names a crashing solver as the sign of
+ * instability; a stalled copy is the other way a step can fail): every time
+ * the step kernel waits for a row it has staged into shared memory with a
+ * bulk copy, it waits at most `ns` nanoseconds (default 10^9, the maximum).
+ * On expiry the warp stops, lets its copies still in flight land (that drain
+ * keeps the one-second bound whatever the limit) and raises a flag, which
+ * lbm_residual reports as LBM_E_CUDA; the fields are then incomplete, and
+ * loading a state (lbm_set_moments / lbm_set_state) clears the flag.  A limit
+ * of 0 makes every such wait give up at once without looking, which tests
+ * this path without any fault.  Errors: LBM_E_INVAL (ns < 0 or > 10^9).
+ */
+int lbm_set_copy_wait_ns(lbm_ctx *ctx, int64_t ns);
 
 /*
  * Copies the current state to caller-owned host arrays of nx*ny doubles:
@@ -213,21 +246,26 @@ int lbm_residual(lbm_ctx *ctx, double *residual, double *mass);
  * elements) into a second caller-owned set, with the node types in a
  * caller-owned uint8 array of the same pitch.  It calls no cudaMalloc,
  * cudaFree or allocating library routine: the reduction scratch is a
- * file-scope device array of 1.5 MB (2^16 blocks x 3 doubles) that every GPU
- * loading this library holds until the process exits.
+ * file-scope device array of 6 MB (2^16 block tiles x 4 warp tiles x 3
+ * doubles, plus the flag) that every GPU loading this library holds until
+ * the process exits.
  *   Inputs:  drho_in, jx_in, jy_in, mask (all 16-byte aligned; pitch >= nx,
- *            the values held at solid nodes are never read;
  *            pitch % 32 == 0; the mask buffer needs 256 bytes of slack after
  *            its last row, which bulk copies of aligned windows may read).
+ *            What the fields hold at solid nodes never reaches a fluid node.
  *   Outputs: drho_out, jx_out, jy_out (same layout; columns nx..pitch-1 may be
- *            overwritten), dev_sums = device array of 3 doubles receiving
+ *            overwritten; fluid nodes get the step, fixed nodes their input
+ *            values, solid nodes an unspecified value), dev_sums = device
+ *            array of 3 doubles receiving
  *            sum |u_n - u_{n-1}|^2, sum |u_n|^2 and sum (rho_n - 1) over fluid
  *            nodes, dev_flags = device uint32 receiving 0 or a nonzero flag
  *            (bit 0: rho <= 0 or a non-finite moment; bit 1: a bulk row copy
  *            did not complete within one second).
  * Asynchronous on cuda_stream.  The first call on each device resolves the
- * scratch array's device address (cudaGetSymbolAddress) and configures the
- * kernel; make that first call before any stream capture.  All calls share
+ * scratch array's device address (cudaGetSymbolAddress); the first step of
+ * the process (through any entry point) configures the kernels once, for the
+ * device current then, so the library serves one device per process.  Make
+ * the first call before any stream capture.  All calls share
  * the one scratch array, so calls that overlap on the GPU (for instance on
  * two streams) race; the array keeps the last call's contents, and the call
  * clears what must start at zero.
@@ -242,7 +280,8 @@ int lbm_step_noalloc(const float *drho_in, const float *jx_in,
                      double *dev_sums, uint32_t *dev_flags, void *cuda_stream);
 
 /* Frees the context's host state and its captured step graphs; the
- * workspace stays the caller's. */
+ * workspace stays the caller's.  (Host bookkeeping: the paper has no
+ * counterpart.) */
 void lbm_destroy(lbm_ctx *ctx);
 
 /*

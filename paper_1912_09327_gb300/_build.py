@@ -17,7 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "liblbmtau1.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["lbm_step.cu", "lbm_api.cu", "lbm_noalloc.cu", "lbm_batch.cu"]
+SOURCES = ["lbm_step_f32.cu", "lbm_step_f16.cu", "lbm_step_bf16.cu",
+           "lbm_step.cu", "lbm_api.cu", "lbm_noalloc.cu", "lbm_batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

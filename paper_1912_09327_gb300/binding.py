@@ -27,9 +27,11 @@ LBM_STORAGE_F16 = 1
 LBM_STORAGE_BF16 = 2
 STORAGE_NAMES = {"f32": LBM_STORAGE_F32, "f16": LBM_STORAGE_F16,
                  "bf16": LBM_STORAGE_BF16}
-LBM_ROUND_STOCHASTIC = 0
+LBM_ROUND_DEFAULT = 0      # 16-bit: stochastic, FP32: nearest
 LBM_ROUND_NEAREST = 1
-ROUNDING_NAMES = {"stochastic": LBM_ROUND_STOCHASTIC,
+LBM_ROUND_STOCHASTIC = 2
+ROUNDING_NAMES = {"default": LBM_ROUND_DEFAULT,
+                  "stochastic": LBM_ROUND_STOCHASTIC,
                   "nearest": LBM_ROUND_NEAREST}
 # host dtype of the exact state transfers (bfloat16 as raw 16-bit words)
 STATE_DTYPE = {LBM_STORAGE_F32: np.float32, LBM_STORAGE_F16: np.float16,
@@ -71,6 +73,8 @@ _lib.lbm_set_variant.argtypes = [_vp, ctypes.c_int32]
 _lib.lbm_set_variant.restype = ctypes.c_int
 _lib.lbm_variant.argtypes = [_vp]
 _lib.lbm_variant.restype = ctypes.c_int32
+_lib.lbm_set_copy_wait_ns.argtypes = [_vp, ctypes.c_int64]
+_lib.lbm_set_copy_wait_ns.restype = ctypes.c_int
 _lib.lbm_moments.argtypes = [_vp, _vp, _vp, _vp]
 _lib.lbm_moments.restype = ctypes.c_int
 _lib.lbm_get_state.argtypes = [_vp, _vp, _vp, _vp]
@@ -145,7 +149,7 @@ def _check(status, ctx=None):
 
 def make_params(nx, ny, periodic=(False, False), force=(0.0, 0.0),
                 storage=LBM_STORAGE_F32,
-                rounding=LBM_ROUND_STOCHASTIC) -> lbm_params:
+                rounding=LBM_ROUND_DEFAULT) -> lbm_params:
     if isinstance(rounding, str):
         rounding = ROUNDING_NAMES[rounding]
     return lbm_params(int(nx), int(ny), int(bool(periodic[0])),
@@ -209,6 +213,11 @@ def lbm_set_variant(ctx, variant: int) -> None:
 
 def lbm_variant(ctx) -> int:
     return int(_lib.lbm_variant(ctx))
+
+
+def lbm_set_copy_wait_ns(ctx, ns: int) -> None:
+    """Wait limit of the step kernel for a staged row copy (0 .. 1e9 ns)."""
+    _check(_lib.lbm_set_copy_wait_ns(ctx, int(ns)), ctx)
 
 
 def lbm_moments(ctx, rho, jx, jy) -> None:
@@ -411,7 +420,7 @@ class Domain:
 
     def __init__(self, nx, ny, periodic=(False, False), force=(0.0, 0.0),
                  device="cuda", stream=None, storage=LBM_STORAGE_F32,
-                 rounding=LBM_ROUND_STOCHASTIC):
+                 rounding=LBM_ROUND_DEFAULT):
         import torch
         self.nx, self.ny = int(nx), int(ny)
         if isinstance(storage, str):
@@ -447,6 +456,9 @@ class Domain:
 
     def set_variant(self, v):
         lbm_set_variant(self.ctx, v)
+
+    def set_copy_wait_ns(self, ns):
+        lbm_set_copy_wait_ns(self.ctx, ns)
 
     def step_count(self):
         return lbm_step_count(self.ctx)

@@ -31,8 +31,9 @@ bool params_ok(const lbm_params *p) {
          p->ny <= kMaxExtent &&
          (p->storage == LBM_STORAGE_F32 || p->storage == LBM_STORAGE_F16 ||
           p->storage == LBM_STORAGE_BF16) &&
-         (p->rounding == LBM_ROUND_STOCHASTIC ||
-          p->rounding == LBM_ROUND_NEAREST) &&
+         (p->rounding == LBM_ROUND_DEFAULT ||
+          p->rounding == LBM_ROUND_NEAREST ||
+          p->rounding == LBM_ROUND_STOCHASTIC) &&
          isfinite(p->fx) && isfinite(p->fy);
 }
 
@@ -164,6 +165,7 @@ int lbm_create(const lbm_params *p, void *dev_workspace, size_t workspace_bytes,
   c->graph_variant[0] = c->graph_variant[1] = -1;
   c->graphs_off = cuda_stream == nullptr || c->stream == cudaStreamLegacy ||
                   c->stream == cudaStreamPerThread;
+  c->wait_ns = 1000000000ull;
   c->has_geometry = false;
   c->has_residual = false;
   c->n_fluid = 0;
@@ -419,8 +421,8 @@ int lbm_step(lbm_ctx *c, int64_t nsteps) {
     c->clean_variant = c->variant;
   }
   a.clean = c->clean;
-  a.sr = c->p.storage != LBM_STORAGE_F32 &&
-         c->p.rounding == LBM_ROUND_STOCHASTIC;
+  a.wait_ns = c->wait_ns;
+  a.sr = lbmtau1::stochastic_rounding(c->p.storage, c->p.rounding);
   // Steps 1 .. nsteps - 2 go in captured graph chunks when the rounding
   // draws no per-step random bits (the graph replays fixed launch arguments);
   // the first step of each call (any one-time kernel set-up stays outside a
@@ -468,6 +470,17 @@ int lbm_set_variant(lbm_ctx *c, int32_t variant) {
   if (variant < -1 || variant >= lbmtau1::variant_count())
     return fail(c, LBM_E_INVAL, "variant %d out of range", int(variant));
   c->variant = variant;
+  return LBM_OK;
+}
+
+int lbm_set_copy_wait_ns(lbm_ctx *c, int64_t ns) {
+  if (!c) return LBM_E_INVAL;
+  if (ns < 0 || ns > 1000000000ll)
+    return fail(c, LBM_E_INVAL, "copy wait limit %lld ns out of range",
+                static_cast<long long>(ns));
+  c->wait_ns = static_cast<unsigned long long>(ns);
+  // captured graphs hold the old limit in their launch arguments
+  c->graph_variant[0] = c->graph_variant[1] = -1;
   return LBM_OK;
 }
 
@@ -528,7 +541,8 @@ int lbm_residual(lbm_ctx *c, double *residual, double *mass) {
   memcpy(&flag, &h[3], sizeof flag);
   if (flag & 2u)
     return fail(c, LBM_E_CUDA,
-                "a step's bulk row copy did not complete within one second");
+                "a step's bulk row copy did not complete within the wait "
+                "limit (%llu ns)", c->wait_ns);
   const double num = h[0], den = h[1];
   if (residual) *residual = den > 0.0 ? sqrt(num / den) : sqrt(num);
   if (mass) *mass = static_cast<double>(c->n_fluid) + h[2];

@@ -136,8 +136,7 @@ int upload(lbm_batch *b) {
     m.gx = (c->p.nx + tx - 1) / tx;
     m.nblocks = m.gx * ((c->p.ny + ty - 1) / ty);
     m.cur = c->cur;
-    m.sr = c->p.storage != LBM_STORAGE_F32 &&
-           c->p.rounding == LBM_ROUND_STOCHASTIC;
+    m.sr = lbmtau1::stochastic_rounding(c->p.storage, c->p.rounding);
     m.step_base = c->steps - static_cast<int64_t>(b->clock);
     if (c->clean_variant != b->variant) {  // clean-tile flags for our tiles
       cudaError_t e = lbmtau1::launch_tile_flags(

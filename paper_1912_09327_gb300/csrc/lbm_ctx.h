@@ -11,6 +11,13 @@
 
 namespace lbmtau1 {
 
+// Whether a context rounds its stored moments stochastically: always for
+// LBM_ROUND_STOCHASTIC, for the 16-bit formats under LBM_ROUND_DEFAULT.
+inline bool stochastic_rounding(int storage, int rounding) {
+  return rounding == LBM_ROUND_STOCHASTIC ||
+         (rounding == LBM_ROUND_DEFAULT && storage != LBM_STORAGE_F32);
+}
+
 struct Layout {
   int64_t pitch = 0, staging_rows = 0, nblocks = 0;
   size_t field_bytes = 0;   // one field plane
@@ -46,6 +53,7 @@ struct lbm_ctx {
   cudaGraphExec_t graph[2];
   int graph_variant[2];
   bool graphs_off;
+  unsigned long long wait_ns;  // staged-row wait limit of the step kernel
   bool has_geometry;
   bool has_residual;
   int64_t n_fluid;

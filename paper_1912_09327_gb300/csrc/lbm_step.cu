@@ -1,993 +1,9 @@
-// LBMTau1 D2Q9 stream-and-collide step for sm_103a (Matyka & Dzikowski,
-// arXiv:1912.09327, Section 2, Algorithm 1).
-//
-// What one step computes, for every fluid node O (Eqs. rhotau1, utau1 with
-// the equilibrium of Eq. maxwellboltzmann and the wall rule of Eq. feqnoslip):
-//   rho'(O) = sum_k f_k,   j'(O) = sum_k c_k f_k,   c_k = -e_k,
-//   f_k = f^eq_{c_k}(rho(P), (j(P) + F) / rho(P))   if P = O + e_k is not solid,
-//   f_k = w_k rho(O)                                if P is solid.
-// Solid and fixed nodes keep their values.
-//
-// Arithmetic form.  The device stores delta = rho - 1 and j.  With
-// Pi = j' j'^T / rho (j' = j + F) the equilibrium of a source P seen along c is
-//   f^eq_c = w_c (1 + delta + 3 c.j' + 4.5 c^T Pi c - 1.5 tr Pi),
-// so each source contributes a fixed linear combination of six per-node
-// quantities (delta, j', Pi) to its nine receivers: the moments-only closed
-// form that Section 4 derives by multiplying Eq. (LBMTau1) with the raw-moment
-// matrix.  The constant "1" parts sum to exactly 1 (mass) and 0 (momentum),
-// so they are dropped.  The momentum is updated in increment form,
-//   j'(O) = j(O) + (F + sum_k w_k c_k [3 c_k.(j_P - j_O) + ...]),
-// with every j_P - j_O taken as an exact FP32 difference before it is
-// weighted, so the O(|j|) part of the sum is never rounded: the result then
-// carries one rounding of j per step, the floor set by FP32 storage.  A solid
-// source enters with delta_P = delta_O, j'_P = 0 and Pi_P = 0, which is
-// Eq. (feqnoslip) in this form.
-//
-// Kernel structure (HBM-bound stencil; no tensor cores).  A block stacks four
-// warp tiles of 30 kC columns x kRows rows.  Lane l holds kC adjacent columns
-// (one vector per field), so lanes 1..30 own the outputs and lanes 0 and 31
-// carry the one-column halos.  Each warp marches down its tile two source
-// rows at a time; all per-node arithmetic runs on (row r, row r+1) pairs with
-// the packed FP32 instructions (FADD2 / FMUL2 / FFMA2).  Each source row is
-// read from HBM once, turned into per-node quantities once (one reciprocal per
-// node), its left/right neighbour columns come from warp shuffles, and its
-// contributions are added to the output rows it feeds (above, same, below);
-// two output rows complete per pair and are stored as vectors.  Interior warp
-// tiles stream their row windows through a ring of shared-memory stages
-// filled by bulk asynchronous copies (cp.async.bulk completing on mbarriers,
-// every wait bounded in time), several rows ahead of use; at the domain's
-// edges the copies are clipped to the row and a periodic axis's wrapped
-// column arrives as one more 16-byte block.  On the last step of an lbm_step call the
-// same kernel reduces sum |du|^2, sum |u|^2 and sum delta (warp shuffles, one
-// FP64 partial per warp tile) and raises a sticky flag on rho <= 0 or
-// non-finite values.
-// The storage type T (FP32, or FP16 / BF16 deviations) only changes loads and
-// stores; the arithmetic is FP32 throughout.  A batched kernel runs the same
-// tile code, warp by warp, over a work list of many domains' warp tiles.
-#include <cuda_bf16.h>
-#include <cuda_fp16.h>
-#include <float.h>
-#include <math.h>
-#include <stdint.h>
-#include <stdlib.h>
-
-#include <type_traits>
-
-#include "lbm_step.cuh"
+// Dispatch of the LBMTau1 step kernels over the storage formats, and the
+// kernels that do not depend on the format (tile flags, reductions).
+#include "lbm_kernels.cuh"
 
 namespace lbmtau1 {
 namespace {
-
-constexpr int kLanes = 32;
-constexpr int kWarps = kTileWarps;            // warps per block, stacked in y
-constexpr int kThreads = kWarps * kLanes;
-constexpr unsigned kFull = 0xffffffffu;
-
-// D2Q9 weights (rest 4/9, axis 1/9, diagonal 1/36) and the combinations of
-// them that appear in the closed form.
-constexpr float k4_9 = 4.0f / 9.0f;
-constexpr float k1_9 = 1.0f / 9.0f;
-constexpr float k1_36 = 1.0f / 36.0f;
-constexpr float k1_12 = 1.0f / 12.0f;  // 3 * (1/36)
-constexpr float k1_3 = 1.0f / 3.0f;    // 3 * (1/9)
-constexpr float k1_6 = 1.0f / 6.0f;    // 2 * (1/12)
-
-// v mod n in [0, n); one period out (the usual case) costs no division.
-__device__ __forceinline__ int64_t wrap_index(int64_t v, int64_t n) {
-  v = v < 0 ? v + n : (v >= n ? v - n : v);
-  if (v < 0 || v >= n) {
-    v %= n;
-    if (v < 0) v += n;
-  }
-  return v;
-}
-
-// Packed FP32 arithmetic (sm_100 family FADD2 / FMUL2 / FFMA2): every value
-// below is a pair (row r, row r + 1) of the same column.
-__device__ __forceinline__ float2 bc(float a) { return make_float2(a, a); }
-__device__ __forceinline__ float2 add(float2 a, float2 b) {
-  return __fadd2_rn(a, b);
-}
-__device__ __forceinline__ float2 mul(float2 a, float2 b) {
-  return __fmul2_rn(a, b);
-}
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
-  return __ffma2_rn(a, b, c);
-}
-// a - b, rounded once (exact when a and b are within a factor of 2)
-__device__ __forceinline__ float2 sub(float2 a, float2 b) {
-  return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
-}
-
-// Storage formats.  All arithmetic is FP32; a 16-bit format stores the
-// deviations rho - 1 and j scaled by exact powers of two (FP16: 2^10 and 2^6,
-// which keep typical values, |rho - 1| >= 1e-7 and |j| >= 1e-6, out of the
-// subnormal range; BF16 has FP32's exponent range and needs none).
-template <typename T>
-struct Storage;
-template <>
-struct Storage<float> {
-  static constexpr float kD = 1.0f, kJ = 1.0f;
-  __device__ static float decode(float v) { return v; }
-  __device__ static float encode(float v) { return v; }
-};
-template <>
-struct Storage<__half> {
-  static constexpr float kD = 1024.0f, kJ = 64.0f;
-  __device__ static float decode(__half v) { return __half2float(v); }
-  __device__ static __half encode(float v) { return __float2half_rn(v); }
-};
-template <>
-struct Storage<__nv_bfloat16> {
-  static constexpr float kD = 1.0f, kJ = 1.0f;
-  __device__ static float decode(__nv_bfloat16 v) { return __bfloat162float(v); }
-  __device__ static __nv_bfloat16 encode(float v) {
-    return __float2bfloat16_rn(v);
-  }
-};
-
-// kC consecutive elements as one vector load / store.
-template <int kC, typename T>
-struct Vec {
-  static constexpr int kBytes = kC * static_cast<int>(sizeof(T));
-  using type = typename std::conditional<
-      kBytes == 16, uint4,
-      typename std::conditional<kBytes == 8, uint2, unsigned>::type>::type;
-};
-
-// Loads kC elements at p (vector-aligned) and decodes them, times `inv`.
-template <int kC, typename T>
-__device__ __forceinline__ void load_vec(const T *p, float (&o)[kC], float inv,
-                                         bool global) {
-  using V = typename Vec<kC, T>::type;
-  union {
-    V v;
-    T e[kC];
-  } u;
-  u.v = global ? __ldg(reinterpret_cast<const V *>(p))
-               : *reinterpret_cast<const V *>(p);
-#pragma unroll
-  for (int j = 0; j < kC; ++j) o[j] = Storage<T>::decode(u.e[j]) * inv;
-}
-
-// Encodes kC values times `scale` and stores them as one vector.
-template <int kC, typename T>
-__device__ __forceinline__ void store_vec(T *p, const float (&v)[kC],
-                                          float scale) {
-  using V = typename Vec<kC, T>::type;
-  union {
-    V v;
-    T e[kC];
-  } u;
-#pragma unroll
-  for (int j = 0; j < kC; ++j) u.e[j] = Storage<T>::encode(v[j] * scale);
-  *reinterpret_cast<V *>(p) = u.v;
-}
-
-// ---- Stochastic rounding of the 16-bit formats ----
-// Random bits from a counter-based hash: the 32-bit finaliser of Appleby's
-// MurmurHash3 (a bijection of 32-bit words with full avalanche), applied to
-// the step count, then the row, then (column, field).
-__device__ __forceinline__ uint32_t fmix32(uint32_t h) {
-  h ^= h >> 16;
-  h *= 0x85ebca6bu;
-  h ^= h >> 13;
-  h *= 0xc2b2ae35u;
-  h ^= h >> 16;
-  return h;
-}
-
-// Two FP32 values to one packed pair, each rounded up or down at random with
-// the probability that makes its expected value exact (cvt.rs, sm_100
-// family); `lo` lands in the low half (the lower address).
-__device__ __forceinline__ uint32_t pack_sr(__half, float lo, float hi,
-                                            uint32_t bits) {
-  uint32_t d;
-  asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(bits));
-  return d;
-}
-__device__ __forceinline__ uint32_t pack_sr(__nv_bfloat16, float lo, float hi,
-                                            uint32_t bits) {
-  uint32_t d;
-  asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(bits));
-  return d;
-}
-
-// store_vec with stochastic rounding; `key` identifies (row, step, field) and
-// `x` is the first column (each pair of columns draws one hashed word).
-template <int kC, typename T>
-__device__ __forceinline__ void store_vec_sr(T *p, const float (&v)[kC],
-                                             float scale, uint32_t key,
-                                             uint32_t x) {
-  static_assert(kC % 2 == 0, "pairs of columns");
-  uint32_t w[kC / 2];
-#pragma unroll
-  for (int q = 0; q < kC / 2; ++q)
-    w[q] = pack_sr(T(), v[2 * q] * scale, v[2 * q + 1] * scale,
-                   fmix32(key + (x + 2u * q) * 0x9e3779b1u));
-  if constexpr (kC == 4)
-    *reinterpret_cast<uint2 *>(p) = make_uint2(w[0], w[1]);
-  else
-    *reinterpret_cast<uint32_t *>(p) = w[0];
-}
-
-// One source row as loaded: kC columns of raw fields and their node types.
-template <int kC>
-struct RawRow {
-  float d[kC], jx[kC], jy[kC];
-  unsigned solid;  // bit j: column j is solid or outside a non-periodic edge
-  unsigned fluid;  // bit j: column j is a fluid node
-};
-
-// gathers bit 0 of each of the kC low bytes of v into bits 0..kC-1
-template <int kC>
-__device__ __forceinline__ unsigned byte_bits(unsigned v) {
-  if constexpr (kC == 4) {
-    v &= 0x01010101u;
-    return (v | (v >> 7) | (v >> 14) | (v >> 21)) & 0xFu;
-  } else {
-    v &= 0x0101u;
-    return (v | (v >> 7)) & 0x3u;
-  }
-}
-
-// ---- Row staging through shared memory with the bulk-copy (TMA) engine ----
-// Every warp tile streams its source rows through a ring of kS shared-memory
-// stages: lane 0 starts `cp.async.bulk` global->shared copies of the tile's
-// row window (three fields and the node types) several rows ahead, each
-// completing on the stage's mbarrier, so the loads in flight do not occupy
-// registers.  Every wait is bounded in time; on expiry the kernel raises
-// kFlagCopyTimeout, drains its copies (again bounded) and stops.
-constexpr unsigned kFlagUnstable = 1u;
-constexpr unsigned kFlagCopyTimeout = 2u;
-constexpr unsigned long long kWaitLimitNs = 1000000000ull;  // one second
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar))
-               : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
-                   smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ void mbar_inval(uint64_t *bar) {
-  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
-}
-
-// completes the current phase without data (a stage use that copies nothing)
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar))
-               : "memory");
-}
-
-__device__ __forceinline__ void bulk_copy(void *dst, const void *src,
-                                          uint32_t bytes, uint64_t *bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes "
-      "[%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
-  uint32_t done;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(done)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return done != 0u;
-}
-
-// Waits for phase `parity` of `bar`; false when a second passes first.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-  if (mbar_try(bar, parity)) return true;
-  const unsigned long long t0 = global_ns();
-  while (!mbar_try(bar, parity))
-    if (global_ns() - t0 > kWaitLimitNs) return false;
-  return true;
-}
-
-__device__ __forceinline__ void fence_async_shared() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-// Geometry of one ring stage for kC columns per lane: the field window starts
-// at ws, the 16-byte boundary at or below the warp's first column x0 - kC,
-// and covers its kLanes * kC columns; the node-type window starts at the
-// 16-byte boundary at or below ws.  A side slot after them holds, on a
-// periodic x axis, the 16-byte blocks (three fields, node types) that start
-// the row: column nx seen from the domain's last column.
-template <int kC, typename T>
-struct Stage {
-  static constexpr int kAlignElems = 16 / static_cast<int>(sizeof(T));
-  static constexpr int kWin =
-      (kAlignElems - 1 + kLanes * kC + kAlignElems - 1) / kAlignElems * kAlignElems;
-  static constexpr int kFieldBytes = kWin * static_cast<int>(sizeof(T));
-  static constexpr int kMaskBytes = (kWin + 15 + 15) / 16 * 16;
-  static constexpr int kSideBytes = 4 * 16;
-  static constexpr int kBytes = 3 * kFieldBytes + kMaskBytes + kSideBytes;
-};
-
-// Sums of w_k (1, c_k) over the solid neighbours of a node, indexed by the
-// 3 x 3 solid bits around it: bits 0-2 the row below (SW, S, SE), 3-5 its own
-// row (W, -, E), 6-8 the row above (NW, N, NE).  c_k = -e_k points from the
-// neighbour to the node.
-struct alignas(16) SolidSums {
-  float s0, sx, sy, pad;
-};
-
-__device__ __forceinline__ void build_solid_lut(SolidSums *lut) {
-  for (int c = threadIdx.x; c < 512; c += blockDim.x) {
-    const float sw = (c >> 0) & 1, s = (c >> 1) & 1, se = (c >> 2) & 1;
-    const float w = (c >> 3) & 1, e = (c >> 5) & 1;
-    const float nw = (c >> 6) & 1, n = (c >> 7) & 1, ne = (c >> 8) & 1;
-    SolidSums v;
-    v.s0 = k1_9 * ((w + e) + (s + n)) + k1_36 * ((sw + se) + (nw + ne));
-    v.sx = k1_9 * (w - e) + k1_36 * ((sw - se) + (nw - ne));
-    v.sy = k1_9 * (s - n) + k1_36 * ((sw + se) - (nw + ne));
-    v.pad = 0.f;
-    lut[c] = v;
-  }
-}
-
-// The step kernel.  kC columns per lane (4: float4 rows, 2: float2 rows);
-// kRows output rows per warp (even).  Source rows arrive in pairs (r, r+1)
-// and all per-node arithmetic runs on (row r, row r+1) float2 pairs.
-//
-// With S = (r, r+1) and S' = (r-2, r-1) the previous pair, each pair adds
-//   North(S) to output rows (r-1, r), Same(S) to rows (r, r+1) and
-//   South(S) to rows (r+1, r+2),
-// so rows (r-1, r) are complete after pair S:
-//   out(r-1) = North(S).x + Same(S').y + South(S').x,
-//   out(r)   = North(S).y + Same(S).x  + South(S').y.
-template <typename T, int kC, int kS>
-__host__ __device__ constexpr int ring_bytes() {
-  return 128 + kS * Stage<kC, T>::kBytes;  // barriers, then the stages
-}
-
-template <typename T, int kC, int kS>
-__host__ __device__ constexpr int smem_bytes() {
-  return 512 * static_cast<int>(sizeof(SolidSums)) +
-         kWarps * ring_bytes<T, kC, kS>();
-}
-
-// One warp tile of a step: warp w (0 .. kWarps - 1, stacked in y) of block
-// tile (bx, by), (30 kC) columns x kRows rows.  `gx` is the number of block
-// tiles along x (for the index of the warp's reduction partial); `slot` is
-// the calling warp's place in its block, which owns a shared-memory ring.
-// Every lane of the warp calls it; no other warp takes part.  kClean: the
-// warp tile's marched rows and columns all lie inside the domain and hold
-// fluid nodes only (see tile_flags_kernel), so node types, edges and wall
-// terms need no handling and the node-type rows are not copied.
-template <typename T, int kC, int kRows, int kS, bool kReduce, bool kClean>
-__device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
-                                          int64_t by, int w, int slot,
-                                          int64_t gx, const SolidSums *lut,
-                                          unsigned char *smem) {
-  static_assert(kRows % 2 == 0, "rows per warp must be even");
-  static_assert(kS >= 4 && kS % 2 == 0 && kS <= 16, "ring stages");
-  constexpr int kTile = (kLanes - 2) * kC;
-  using St = Stage<kC, T>;
-  using SS = Storage<T>;
-
-  const int lane = threadIdx.x & (kLanes - 1);
-  const int64_t x0 = bx * kTile;
-  const int64_t xb = x0 - kC + static_cast<int64_t>(kC) * lane;
-  const int64_t y0 = (by * kWarps + w) * kRows;
-  const int64_t y1 = min(y0 + kRows, a.ny);
-  const bool owner = lane >= 1 && lane <= kLanes - 2 && xb < a.nx;
-  // columns of this lane that are outputs inside the domain (reductions)
-  unsigned out_cols = 0u;
-#pragma unroll
-  for (int j = 0; j < kC; ++j) out_cols |= (owner && xb + j < a.nx) << j;
-  // Row windows.  Of the field window [ws, ws + kWin) and the node-type
-  // window [m0, m0 + kMaskBytes), the bulk copies fill the part inside the
-  // row, [c0, c1) and [k0, k1), rounded out to 16-byte boundaries (which stay
-  // inside the row's pitch).  Other columns read as solid, except that on a
-  // periodic x axis column -1 is column nx - 1 and column nx is column 0: the
-  // 16-byte blocks holding those land in the window head (the tile at x = 0
-  // starts its window one block left of the domain) and in the side slot.
-  const int64_t ws = (x0 - kC) & ~int64_t(St::kAlignElems - 1);
-  const int64_t m0 = ws & ~int64_t(15);
-  const bool interior = ws >= 0 && ws + St::kMaskBytes <= a.nx;
-  const bool wrap_l = a.periodic_x && ws < 0;
-  const bool wrap_r = a.periodic_x && a.nx < x0 + (kLanes - 1) * kC;
-  // this lane's columns that lie in the domain, and the one (if any) that is
-  // column -1 or nx of a periodic x axis, read from the wrapped blocks
-  unsigned in_cols = 0u;
-#pragma unroll
-  for (int j = 0; j < kC; ++j)
-    in_cols |= (xb + j >= 0 && xb + j < a.nx) << j;
-  int wrap_col = -1;
-  if (wrap_l && xb < 0) wrap_col = kC - 1;            // column -1
-  if (wrap_r && xb <= a.nx && a.nx < xb + kC)          // column nx
-    wrap_col = static_cast<int>(a.nx - xb);
-  unsigned char *ring =
-      smem + 512 * sizeof(SolidSums) + slot * ring_bytes<T, kC, kS>();
-  uint64_t *bars = reinterpret_cast<uint64_t *>(ring);
-  unsigned char *stages = ring + 128;
-  const int c_lane = static_cast<int>(x0 - kC - ws) + kC * lane;
-  const int m_lane = static_cast<int>(ws - m0) + c_lane;
-  const float fx = a.fx, fy = a.fy;
-  const float2 F2x = bc(fx), F2y = bc(fy), F22y = bc(2.0f * fy);
-  const float2 one = bc(1.0f), c3 = bc(3.0f), cm15 = bc(-1.5f);
-  const float2 w1_9 = bc(k1_9), w1_36 = bc(k1_36), w1_12 = bc(k1_12),
-               w1_3 = bc(k1_3), w4_9 = bc(k4_9), w1_6 = bc(k1_6),
-               wm1_6 = bc(-k1_6), half = bc(0.5f), quarter = bc(0.25f);
-
-  float2 rs_num = bc(0.f), rs_den = bc(0.f), rs_mass = bc(0.f);
-  float rmin = 1.0f;
-
-  if (y0 < a.ny) {
-    // carried from the previous pair S'
-    float same_dd[kC], same_mx[kC];                 // Same(S').y
-    float2 south_dd[kC], south_mx[kC], south_my[kC];  // South(S')
-    float pd[kC], pjx[kC], pjy[kC], pir[kC];        // raw row r-1, its 1/rho
-    float2 zpx[kC], zpy[kC];                        // z of S'
-#pragma unroll
-    for (int j = 0; j < kC; ++j) {
-      same_dd[j] = same_mx[j] = 0.f;
-      south_dd[j] = south_mx[j] = south_my[j] = bc(0.f);
-      pd[j] = pjx[j] = pjy[j] = 0.f;
-      pir[j] = 1.f;
-      zpx[j] = zpy[j] = bc(0.f);
-    }
-    unsigned pA6 = 0u, pB6 = 0u;  // solid bits (cols -1..kC) of rows r-2, r-1
-    unsigned pfluidB = 0u;        // fluid bits of row r-1
-
-    // Row indices in 32 bits: the launchers reject ny >= 2^30.
-    const int ty0 = static_cast<int>(y0), ty1 = static_cast<int>(y1);
-    const int tny = static_cast<int>(a.ny);
-    const int npairs = (ty1 - ty0 + 1) / 2 + 1;
-    const int nrows = 2 * npairs;  // source rows y0 - 1 .. y0 - 2 + nrows
-    // source row of ring index i: -1 for a solid row beyond a wall-less edge
-    auto source_row = [&](int i) -> int {
-      const int r = ty0 - 1 + i;
-      if (r >= 0 && r < tny) return r;
-      return a.periodic_y ? static_cast<int>(wrap_index(r, tny)) : -1;
-    };
-    auto issue = [&](int i) {  // lane 0 only
-      const int r = source_row(i);
-      const int st = static_cast<int>(static_cast<unsigned>(i) % kS);
-      uint64_t *bar = bars + st;
-      if (r < 0) {  // solid row: nothing to copy, but the phase still completes
-        mbar_arrive(bar);
-        return;
-      }
-      unsigned char *dst = stages + st * St::kBytes;
-      unsigned char *dmask = dst + 3 * St::kFieldBytes;
-      if (interior) {  // the whole window lies in the row
-        const int64_t off = static_cast<int64_t>(r) * a.pitch + ws;
-        mbar_expect_tx(bar, 3 * St::kFieldBytes + (kClean ? 0 : St::kMaskBytes));
-        bulk_copy(dst, static_cast<const T *>(a.src.d) + off, St::kFieldBytes,
-                  bar);
-        bulk_copy(dst + St::kFieldBytes,
-                  static_cast<const T *>(a.src.jx) + off, St::kFieldBytes, bar);
-        bulk_copy(dst + 2 * St::kFieldBytes,
-                  static_cast<const T *>(a.src.jy) + off, St::kFieldBytes, bar);
-        if (!kClean)
-          bulk_copy(dmask, a.mask + r * a.pitch + m0, St::kMaskBytes, bar);
-        return;
-      }
-      constexpr int64_t kA = St::kAlignElems;
-      const int64_t c0 = max(ws, int64_t(0));
-      const int64_t c1 = min(ws + St::kWin, (a.nx + kA - 1) & ~(kA - 1));
-      const int64_t k0 = max(m0, int64_t(0));
-      const int64_t k1 = min(m0 + St::kMaskBytes, (a.nx + 15) & ~int64_t(15));
-      const uint32_t fbytes = static_cast<uint32_t>((c1 - c0) * sizeof(T));
-      const uint32_t mbytes = kClean ? 0u : static_cast<uint32_t>(k1 - k0);
-      mbar_expect_tx(bar, 3 * fbytes + mbytes + (wrap_l ? 64u : 0u) +
-                              (wrap_r ? 64u : 0u));
-      const int64_t rp = static_cast<int64_t>(r) * a.pitch;
-      const T *src[3] = {static_cast<const T *>(a.src.d) + rp,
-                         static_cast<const T *>(a.src.jx) + rp,
-                         static_cast<const T *>(a.src.jy) + rp};
-      const uint8_t *mrow = a.mask + rp;
-      const int64_t foff = (c0 - ws) * static_cast<int64_t>(sizeof(T));
-#pragma unroll
-      for (int f = 0; f < 3; ++f)
-        bulk_copy(dst + f * St::kFieldBytes + foff, src[f] + c0, fbytes, bar);
-      if (!kClean) bulk_copy(dmask + (k0 - m0), mrow + k0, mbytes, bar);
-      if (wrap_l) {  // the blocks holding column nx - 1, into the window head
-        const int64_t lf = (a.nx - 1) & ~(kA - 1), lm = (a.nx - 1) & ~int64_t(15);
-#pragma unroll
-        for (int f = 0; f < 3; ++f)
-          bulk_copy(dst + f * St::kFieldBytes, src[f] + lf, 16u, bar);
-        bulk_copy(dmask, mrow + lm, 16u, bar);
-      }
-      if (wrap_r) {  // the blocks holding column 0, into the side slot
-        unsigned char *side = dmask + St::kMaskBytes;
-#pragma unroll
-        for (int f = 0; f < 3; ++f) bulk_copy(side + 16 * f, src[f], 16u, bar);
-        bulk_copy(side + 48, mrow, 16u, bar);
-      }
-    };
-    // ring row i -> registers; false when the copy did not arrive in time
-    auto fetch = [&](int i, RawRow<kC> &o) -> bool {
-      if constexpr (kClean) {  // an in-domain row of fluid nodes
-        const unsigned ui = static_cast<unsigned>(i);
-        const int st = static_cast<int>(ui % kS);
-        const bool ok = mbar_wait(bars + st, (ui / kS) & 1u);
-        const unsigned char *src = stages + st * St::kBytes;
-        load_vec<kC, T>(reinterpret_cast<const T *>(src) + c_lane, o.d,
-                        1.0f / SS::kD, false);
-        load_vec<kC, T>(reinterpret_cast<const T *>(src + St::kFieldBytes) +
-                            c_lane,
-                        o.jx, 1.0f / SS::kJ, false);
-        load_vec<kC, T>(reinterpret_cast<const T *>(src + 2 * St::kFieldBytes) +
-                            c_lane,
-                        o.jy, 1.0f / SS::kJ, false);
-        o.solid = 0u;
-        o.fluid = (1u << kC) - 1u;
-        return ok;
-      }
-      if (source_row(i) < 0) {
-#pragma unroll
-        for (int j = 0; j < kC; ++j) o.d[j] = o.jx[j] = o.jy[j] = 0.f;
-        o.solid = (1u << kC) - 1u;
-        o.fluid = 0u;
-        return true;
-      }
-      const unsigned ui = static_cast<unsigned>(i);
-      const int st = static_cast<int>(ui % kS);
-      const bool ok = mbar_wait(bars + st, (ui / kS) & 1u);
-      const unsigned char *src = stages + st * St::kBytes;
-      const T *fd = reinterpret_cast<const T *>(src);
-      const T *fx_ = reinterpret_cast<const T *>(src + St::kFieldBytes);
-      const T *fy_ = reinterpret_cast<const T *>(src + 2 * St::kFieldBytes);
-      const unsigned char *mw = src + 3 * St::kFieldBytes;
-      load_vec<kC, T>(fd + c_lane, o.d, 1.0f / SS::kD, false);
-      load_vec<kC, T>(fx_ + c_lane, o.jx, 1.0f / SS::kJ, false);
-      load_vec<kC, T>(fy_ + c_lane, o.jy, 1.0f / SS::kJ, false);
-      const unsigned char *mk = mw + m_lane;
-      unsigned m;
-      if constexpr (kC == 4)
-        m = *reinterpret_cast<const unsigned *>(mk);
-      else
-        m = *reinterpret_cast<const unsigned short *>(mk);
-      // columns outside the domain are solid (whatever the window holds)
-      o.solid = byte_bits<kC>(m) | (~in_cols & ((1u << kC) - 1u));
-      o.fluid = byte_bits<kC>(~(m | (m >> 1))) & in_cols;
-      if (wrap_col >= 0) {  // column -1 or nx of a periodic x axis
-        const bool left = wrap_col == kC - 1 && xb < 0;
-        // column nx - 1 in the window head, or column 0 in the side slot
-        const int fo = static_cast<int>((a.nx - 1) & (St::kAlignElems - 1));
-        const T *side = reinterpret_cast<const T *>(mw + St::kMaskBytes);
-        const float d = SS::decode(left ? fd[fo] : side[0]) * (1.0f / SS::kD);
-        const float jx = SS::decode(left ? fx_[fo] : side[St::kAlignElems]) *
-                         (1.0f / SS::kJ);
-        const float jy = SS::decode(left ? fy_[fo] : side[2 * St::kAlignElems]) *
-                         (1.0f / SS::kJ);
-        const unsigned t =
-            left ? mw[(a.nx - 1) & 15] : mw[St::kMaskBytes + 48];
-#pragma unroll
-        for (int j = 0; j < kC; ++j) {
-          if (j == wrap_col) {
-            o.d[j] = d;
-            o.jx[j] = jx;
-            o.jy[j] = jy;
-          }
-        }
-        const unsigned bit = 1u << wrap_col;
-        o.solid = (o.solid & ~bit) | ((t == 1u) ? bit : 0u);
-        o.fluid = (o.fluid & ~bit) | ((t == 0u) ? bit : 0u);
-      }
-      return ok;
-    };
-    int issued = 0;
-    if (lane == 0) {
-      for (int st = 0; st < kS; ++st) mbar_init(bars + st);
-      fence_async_shared();
-      for (; issued < nrows && issued < kS; ++issued) issue(issued);
-    }
-    issued = __shfl_sync(kFull, issued, 0);
-    __syncwarp();
-    bool aborted = false;
-    int consumed = 0;
-    for (int k = 0; k < npairs; ++k) {
-      consumed = 2 * k;
-      const int r = ty0 - 1 + 2 * k;  // S = (r, r+1)
-      const bool row0 = r - 1 >= ty0;         // output row r - 1 is in the tile
-      const bool row1 = r >= ty0 && r < ty1;  // output row r is in the tile
-      RawRow<kC> ra, rb;
-      bool ok = fetch(2 * k, ra);
-      ok = fetch(2 * k + 1, rb) && ok;
-      if (!__all_sync(kFull, ok)) {
-        aborted = true;
-        break;
-      }
-      __syncwarp();  // every lane has read both stages
-      if (lane == 0) {
-        fence_async_shared();
-        for (int t = 0; t < 2 && issued < nrows; ++t, ++issued) issue(issued);
-      }
-      issued = __shfl_sync(kFull, issued, 0);
-
-      // Per-node quantities of S, own columns at index j + 1, pre-scaled by
-      // the lattice weights they meet (K = (delta + A) / 9, G / 36, X / 36
-      // with A = 3 Pxx - 1.5 Pyy, G = delta + 3 tr Pi, X = 9 Pxy), so that
-      // each neighbour combination below is a sum or a difference.
-      float2 K[kC + 2], zx[kC + 2], zy[kC + 2], G[kC + 2], X[kC + 2];
-      float2 P[kC], R0[kC], ir[kC];
-#pragma unroll
-      for (int j = 0; j < kC; ++j) {
-        const bool sa = (ra.solid >> j) & 1u, sb = (rb.solid >> j) & 1u;
-        const float2 zxj = make_float2(sa ? -fx : ra.jx[j], sb ? -fx : rb.jx[j]);
-        const float2 zyj = make_float2(sa ? -fy : ra.jy[j], sb ? -fy : rb.jy[j]);
-        const float2 dfj = make_float2(sa ? 0.f : ra.d[j], sb ? 0.f : rb.d[j]);
-        const float2 mx = add(zxj, F2x);  // j + F, exactly 0 on solid nodes
-        const float2 my = add(zyj, F2y);
-        const float2 rho = add(dfj, one);
-        const float2 irj =
-            make_float2(__fdividef(1.0f, rho.x), __fdividef(1.0f, rho.y));
-        const float2 t = mul(mx, irj);
-        const float2 pxx = mul(t, mx), pxy = mul(t, my);
-        const float2 pyy = mul(mul(my, my), irj);
-        const float2 tr = add(pxx, pyy);
-        zx[j + 1] = zxj;
-        zy[j + 1] = zyj;
-        K[j + 1] = fma2(w1_9, dfj, fma2(w1_3, pxx, mul(wm1_6, pyy)));
-        P[j] = fma2(c3, pyy, fma2(cm15, pxx, dfj));  // delta + 3 Pyy - 1.5 Pxx
-        G[j + 1] = fma2(w1_12, tr, mul(w1_36, dfj));
-        X[j + 1] = mul(quarter, pxy);
-        R0[j] = fma2(cm15, tr, make_float2(ra.d[j], rb.d[j]));
-        ir[j] = irj;
-      }
-      // Halo columns -1 and kC from the neighbouring lanes.
-#define LBM_HALO(q)                                                   \
-  q[0].x = __shfl_up_sync(kFull, q[kC].x, 1);                        \
-  q[0].y = __shfl_up_sync(kFull, q[kC].y, 1);                        \
-  q[kC + 1].x = __shfl_down_sync(kFull, q[1].x, 1);                  \
-  q[kC + 1].y = __shfl_down_sync(kFull, q[1].y, 1);
-      LBM_HALO(K)
-      LBM_HALO(zx)
-      LBM_HALO(zy)
-      LBM_HALO(G)
-      LBM_HALO(X)
-#undef LBM_HALO
-      unsigned A6 = 0u, B6 = 0u;
-      bool any_solid = false;
-      if constexpr (!kClean) {
-        const unsigned sbits = ra.solid | (rb.solid << kC);
-        const unsigned sl = __shfl_up_sync(kFull, sbits, 1);
-        const unsigned sr = __shfl_down_sync(kFull, sbits, 1);
-        A6 = ((sl >> (kC - 1)) & 1u) | (ra.solid << 1) |
-             ((sr & 1u) << (kC + 1));
-        B6 = ((sl >> (2 * kC - 1)) & 1u) | (rb.solid << 1) |
-             (((sr >> kC) & 1u) << (kC + 1));
-        any_solid = __any_sync(kFull, (pA6 | pB6 | A6 | B6) != 0u);
-      }
-
-      float od0[kC], ox0[kC], oy0[kC], od1[kC], ox1[kC], oy1[kC];
-      const bool acc_pair = owner && k > 0;  // clean tiles: outputs to sum
-#pragma unroll
-      for (int j = 0; j < kC; ++j) {
-        const int L = j, C = j + 1, R = j + 2;
-        const float2 Gs = add(G[L], G[R]), Gd = sub(G[L], G[R]);
-        const float2 Xs = add(X[L], X[R]), Xd = sub(X[L], X[R]);
-        const float2 mxd = sub(zx[L], zx[R]), myd = sub(zy[L], zy[R]);
-        const float2 mys = add(add(zy[L], zy[R]), F22y);
-        const float2 hx = add(sub(zx[L], zx[C]), sub(zx[R], zx[C]));  // exact
-        const float2 hy = add(sub(zy[L], zy[C]), sub(zy[R], zy[C]));
-        // S as the row pair above output rows (r-1, r), N: NW, N, NE, and
-        // below them (r+1, r+2), T: SW, S, SE.  The two share their terms
-        // up to signs:
-        //   U = P/9 + Gs + mxd/12,  V = (zy_C + Fy)/3 + Xd + mys/12,
-        //   Y = Xd + hy/12,  U' = Gd + hx/12,  V' = Xs + myd/12,
-        //   N = (U - V, U' - V', Y - U),  T = (U + V, U' + V', Y + U)
-        // for (delta, jx, jy).
-        const float2 U = fma2(w1_9, P[j], fma2(w1_12, mxd, Gs));
-        const float2 V = fma2(w1_3, add(zy[C], F2y), fma2(w1_12, mys, Xd));
-        const float2 Y = fma2(w1_12, hy, Xd);
-        const float2 Up = fma2(w1_12, hx, Gd), Vp = fma2(w1_12, myd, Xs);
-        const float2 Ndd = sub(U, V), Tdd = add(U, V);
-        const float2 Nmx = sub(Up, Vp), Tmx = add(Up, Vp);
-        const float2 Nmy = sub(Y, U), Tmy = add(Y, U);
-        // S as the own rows of outputs (r, r+1): W, O, E
-        const float2 Sdd =
-            fma2(w4_9, R0[j], fma2(w1_3, mxd, add(K[L], K[R])));
-        const float2 Smx = fma2(w1_3, hx, sub(K[L], K[R]));
-
-        // Complete output rows (r-1, r) of column j.
-        const float2 acc_dd =
-            add(add(Ndd, make_float2(same_dd[j], Sdd.x)), south_dd[j]);
-        const float2 acc_mx =
-            add(add(Nmx, make_float2(same_mx[j], Smx.x)), south_mx[j]);
-        const float2 acc_my = add(Nmy, south_my[j]);
-        const float2 dO = make_float2(pd[j], ra.d[j]);
-        const float2 jxO = make_float2(pjx[j], ra.jx[j]);
-        const float2 jyO = make_float2(pjy[j], ra.jy[j]);
-        // the momentum increments; solid neighbours add their wall terms in
-        // place below (nothing to add, and no zero terms, without solids)
-        float2 dn = acc_dd;
-        float2 incx = fma2(w1_6, add(sub(zpx[j], jxO), sub(zx[C], jxO)),
-                           add(acc_mx, F2x));
-        float2 incy = fma2(half, add(sub(zpy[j], jyO), sub(zy[C], jyO)),
-                           add(acc_my, F2y));
-        if (!kClean && any_solid) {
-          const unsigned c0 = ((pA6 >> j) & 7u) | (((pB6 >> j) & 7u) << 3) |
-                              (((A6 >> j) & 7u) << 6);
-          const unsigned c1 = ((pB6 >> j) & 7u) | (((A6 >> j) & 7u) << 3) |
-                              (((B6 >> j) & 7u) << 6);
-          const SolidSums e0 = lut[c0], e1 = lut[c1];
-          dn = fma2(dO, make_float2(e0.s0, e1.s0), dn);
-          incx = fma2(dO, make_float2(e0.sx, e1.sx), incx);
-          incy = fma2(dO, make_float2(e0.sy, e1.sy), incy);
-        }
-        const float2 mxn = add(jxO, incx);
-        const float2 myn = add(jyO, incy);
-        const bool f0 = kClean || ((pfluidB >> j) & 1u);
-        const bool f1 = kClean || ((ra.fluid >> j) & 1u);
-        od0[j] = f0 ? dn.x : dO.x;
-        ox0[j] = f0 ? mxn.x : jxO.x;
-        oy0[j] = f0 ? myn.x : jyO.x;
-        od1[j] = f1 ? dn.y : dO.y;
-        ox1[j] = f1 ? mxn.y : jxO.y;
-        oy1[j] = f1 ? myn.y : jyO.y;
-        if constexpr (kReduce) {
-          const bool col = (out_cols >> j) & 1u;
-          const bool v0 = f0 && col && row0;
-          const bool v1 = f1 && col && row1;
-          // u_new - u_old = ((j_n - j_o) - u_o (d_n - d_o)) / rho_n: the
-          // step's own changes, no cancellation between two O(|u|) values
-          const float2 rn = add(dn, one);
-          const float2 irn =
-              make_float2(__fdividef(1.0f, rn.x), __fdividef(1.0f, rn.y));
-          const float2 irn2 = mul(irn, irn);
-          const float2 iro = make_float2(pir[j], ir[j].x);
-          const float2 mdd = sub(dO, dn);
-          const float2 ex = fma2(mul(jxO, iro), mdd, sub(mxn, jxO));
-          const float2 ey = fma2(mul(jyO, iro), mdd, sub(myn, jyO));
-          const float2 nn = mul(fma2(ex, ex, mul(ey, ey)), irn2);
-          const float2 dd2 = mul(fma2(mxn, mxn, mul(myn, myn)), irn2);
-          if constexpr (kClean) {
-            // a clean tile is full height with every column in the domain:
-            // both rows count exactly when the pair has outputs.  The packed
-            // sums add the same non-negative terms in the same order as the
-            // scalar ones below; the compiler may fuse a packed scale and add
-            // (one rounding instead of two), so the two agree to float
-            // rounding
-            if (acc_pair) {
-              rs_num = add(rs_num, nn);
-              rs_den = add(rs_den, dd2);
-              rs_mass = add(rs_mass, dn);
-              rmin = fminf(rmin, fminf(rn.x, rn.y));
-            }
-          } else {
-            if (v0) {
-              rs_num.x += nn.x;
-              rs_den.x += dd2.x;
-              rs_mass.x += dn.x;
-              rmin = fminf(rmin, rn.x);
-            }
-            if (v1) {
-              rs_num.y += nn.y;
-              rs_den.y += dd2.y;
-              rs_mass.y += dn.y;
-              rmin = fminf(rmin, rn.y);
-            }
-          }
-        }
-        // carry to the next pair
-        same_dd[j] = Sdd.y;
-        same_mx[j] = Smx.y;
-        south_dd[j] = Tdd;
-        south_mx[j] = Tmx;
-        south_my[j] = Tmy;
-      }
-      bool stored = false;
-      if constexpr (!std::is_same<T, float>::value) {
-        if (a.sr) {  // uniform across the warp
-          stored = true;
-          if (owner) {
-            T *dd = static_cast<T *>(a.dst.d);
-            T *dx = static_cast<T *>(a.dst.jx);
-            T *dy = static_cast<T *>(a.dst.jy);
-            const uint32_t xs = static_cast<uint32_t>(xb);
-            const uint32_t sk = fmix32(a.step);
-            // one key per (row, step); fields offset it by constants
-            auto row_key = [&](int row) {
-              return fmix32(sk ^ (static_cast<uint32_t>(row) * 0x85ebca77u));
-            };
-            if (row0) {
-              const uint32_t key = row_key(r - 1);
-              const int64_t o = static_cast<int64_t>(r - 1) * a.pitch + xb;
-              store_vec_sr<kC, T>(dd + o, od0, SS::kD, key, xs);
-              store_vec_sr<kC, T>(dx + o, ox0, SS::kJ, key + 0x632be5abu, xs);
-              store_vec_sr<kC, T>(dy + o, oy0, SS::kJ, key + 0xc6bc279au, xs);
-            }
-            if (row1) {
-              const uint32_t key = row_key(r);
-              const int64_t o = static_cast<int64_t>(r) * a.pitch + xb;
-              store_vec_sr<kC, T>(dd + o, od1, SS::kD, key, xs);
-              store_vec_sr<kC, T>(dx + o, ox1, SS::kJ, key + 0x632be5abu, xs);
-              store_vec_sr<kC, T>(dy + o, oy1, SS::kJ, key + 0xc6bc279au, xs);
-            }
-          }
-        }
-      }
-      if (owner && !stored) {
-        T *dd = static_cast<T *>(a.dst.d);
-        T *dx = static_cast<T *>(a.dst.jx);
-        T *dy = static_cast<T *>(a.dst.jy);
-        if (row0) {
-          const int64_t o = static_cast<int64_t>(r - 1) * a.pitch + xb;
-          store_vec<kC, T>(dd + o, od0, SS::kD);
-          store_vec<kC, T>(dx + o, ox0, SS::kJ);
-          store_vec<kC, T>(dy + o, oy0, SS::kJ);
-        }
-        if (row1) {
-          const int64_t o = static_cast<int64_t>(r) * a.pitch + xb;
-          store_vec<kC, T>(dd + o, od1, SS::kD);
-          store_vec<kC, T>(dx + o, ox1, SS::kJ);
-          store_vec<kC, T>(dy + o, oy1, SS::kJ);
-        }
-      }
-      // Shift the window by one pair.
-#pragma unroll
-      for (int j = 0; j < kC; ++j) {
-        pd[j] = rb.d[j];
-        pjx[j] = rb.jx[j];
-        pjy[j] = rb.jy[j];
-        pir[j] = ir[j].y;
-        zpx[j] = zx[j + 1];
-        zpy[j] = zy[j + 1];
-      }
-      pA6 = A6;
-      pB6 = B6;
-      pfluidB = rb.fluid;
-    }
-    if (aborted) {
-      if (lane == 0) atomicOr(a.flag, kFlagCopyTimeout);
-      // let every copy still in flight land before the block exits
-      for (int i = consumed; i < issued; ++i) {
-        if (source_row(i) < 0) continue;
-        const unsigned ui = static_cast<unsigned>(i);
-        mbar_wait(bars + ui % kS, (ui / kS) & 1u);
-      }
-    }
-    // release the barriers so the ring can serve another tile
-    __syncwarp();
-    if (lane == 0)
-      for (int st = 0; st < kS; ++st) mbar_inval(bars + st);
-    __syncwarp();
-  }
-
-  if constexpr (kReduce) {
-    double v0 = static_cast<double>(rs_num.x) + rs_num.y;
-    double v1 = static_cast<double>(rs_den.x) + rs_den.y;
-    double v2 = static_cast<double>(rs_mass.x) + rs_mass.y;
-#pragma unroll
-    for (int o = kLanes / 2; o > 0; o >>= 1) {
-      v0 += __shfl_xor_sync(kFull, v0, o);
-      v1 += __shfl_xor_sync(kFull, v1, o);
-      v2 += __shfl_xor_sync(kFull, v2, o);
-    }
-    const bool bad = !(rmin > 0.f) || !isfinite(v0) || !isfinite(v1) ||
-                     !isfinite(v2);
-    const bool any_bad = __any_sync(kFull, bad);
-    if (lane == 0) {
-      double *q = a.partials + 3 * ((by * gx + bx) * kWarps + w);
-      q[0] = v0;
-      q[1] = v1;
-      q[2] = v2;
-      if (any_bad) atomicOr(a.flag, kFlagUnstable);
-    }
-  }
-}
-
-// Runs warp tile (bx, by, w).  kDual: with the code for clean tiles when
-// the tile's flag says so (flags absent: the general code); otherwise the
-// general code only, which keeps the kernel's registers for one code path.
-template <typename T, int kC, int kRows, int kS, bool kReduce, bool kDual>
-__device__ __forceinline__ void run_tile(const StepLaunch &a, int64_t bx,
-                                         int64_t by, int w, int slot,
-                                         int64_t gx, const SolidSums *lut,
-                                         unsigned char *smem) {
-  if constexpr (!kDual) {
-    step_tile<T, kC, kRows, kS, kReduce, false>(a, bx, by, w, slot, gx, lut,
-                                                smem);
-    return;
-  }
-  const bool clean = a.clean && a.clean[(by * gx + bx) * kWarps + w];
-  if (clean)
-    step_tile<T, kC, kRows, kS, kReduce, true>(a, bx, by, w, slot, gx, lut,
-                                               smem);
-  else
-    step_tile<T, kC, kRows, kS, kReduce, false>(a, bx, by, w, slot, gx, lut,
-                                                smem);
-}
-
-template <typename T, int kC, int kRows, int kMinBlocks, int kS, bool kReduce,
-          bool kDual>
-__global__ void __launch_bounds__(kThreads, kMinBlocks)
-    lbm_step_kernel(const StepLaunch a) {
-  extern __shared__ __align__(128) unsigned char smem[];
-  SolidSums *lut = reinterpret_cast<SolidSums *>(smem);
-  build_solid_lut(lut);
-  __syncthreads();
-  const int warp = threadIdx.x / kLanes;
-  run_tile<T, kC, kRows, kS, kReduce, kDual>(a, blockIdx.x, blockIdx.y, warp,
-                                             warp, gridDim.x, lut, smem);
-}
-
-// Batched step: a persistent grid whose warps take warp tiles of many domains
-// from one work list through an atomic counter, so that one launch advances
-// every member of a batch by one step.  Each warp works on its own (its own
-// ring, no block barrier between tiles), and tile for tile it runs the same
-// code as the single-domain kernel, so each member's result does not depend
-// on the batch.
-template <typename T, int kC, int kRows, int kMinBlocks, int kS, bool kReduce,
-          bool kDual>
-__global__ void __launch_bounds__(kThreads, kMinBlocks)
-    lbm_batch_kernel(const BatchLaunch b) {
-  extern __shared__ __align__(128) unsigned char smem[];
-  SolidSums *lut = reinterpret_cast<SolidSums *>(smem);
-  build_solid_lut(lut);
-  // the batch clock: read by every block before the last block advances it
-  const unsigned clock = *b.clock;
-  __syncthreads();
-  const int n = *b.nitems;
-  const int slot = threadIdx.x / kLanes;
-  for (;;) {
-    int it = 0;
-    if ((threadIdx.x & (kLanes - 1)) == 0)
-      it = static_cast<int>(atomicAdd(b.counter, 1u));
-    it = __shfl_sync(kFull, it, 0);
-    if (it >= n) break;
-    const int4 w = b.items[it];  // member, tile x, tile y, warp
-    const BatchMember &m = b.members[w.x];
-    const int c = (m.cur ^ b.parity) & 1;
-    StepLaunch a;
-    a.src = m.f[c];
-    a.dst = m.f[1 - c];
-    a.mask = m.mask;
-    a.nx = m.nx;
-    a.ny = m.ny;
-    a.pitch = m.pitch;
-    a.periodic_x = m.periodic_x;
-    a.periodic_y = m.periodic_y;
-    a.fx = m.fx;
-    a.fy = m.fy;
-    a.partials = m.partials;
-    a.flag = m.flag;
-    a.storage = b.storage;
-    a.sr = m.sr;
-    a.step = static_cast<uint32_t>(m.step_base) + clock;
-    a.clean = m.clean;
-    run_tile<T, kC, kRows, kS, kReduce, kDual>(a, w.y, w.z, w.w, slot, m.gx,
-                                               lut, smem);
-  }
-  // the last block to finish advances the clock for the next launch (every
-  // thread read it before its block's first tile)
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    if (atomicAdd(b.done, 1u) == gridDim.x - 1) {
-      *b.done = 0u;
-      *b.clock = clock + 1u;
-      __threadfence();
-    }
-  }
-}
 
 // One warp per warp tile: 1 when the tile is clean (see launch_tile_flags).
 template <int kC, int kRows>
@@ -1092,249 +108,17 @@ __global__ void __launch_bounds__(kFinalizeThreads)
   if (threadIdx.x < 3) out[threadIdx.x] = buf[threadIdx.x][0];
 }
 
-template <typename T>
-__global__ void pack_kernel(const double *__restrict__ staging, Fields f,
-                            int64_t nx, int64_t pitch, int64_t y0,
-                            int64_t rows) {
-  using S = Storage<T>;
-  const int64_t n = nx * rows;
-  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-       i < n; i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const int64_t y = y0 + i / nx, x = i % nx;
-    const int64_t o = y * pitch + x;
-    static_cast<T *>(f.d)[o] =
-        S::encode(static_cast<float>(staging[i] - 1.0) * S::kD);
-    static_cast<T *>(f.jx)[o] =
-        S::encode(static_cast<float>(staging[n + i]) * S::kJ);
-    static_cast<T *>(f.jy)[o] =
-        S::encode(static_cast<float>(staging[2 * n + i]) * S::kJ);
+// the launchers of a storage format
+const StorageOps &ops(int storage) {
+  switch (storage) {
+    case kStorageF16: return kOpsF16;
+    case kStorageBF16: return kOpsBF16;
+    default: return kOpsF32;
   }
-}
-
-template <typename T>
-__global__ void unpack_kernel(Fields f, const uint8_t *__restrict__ mask,
-                              double *__restrict__ staging, int64_t nx,
-                              int64_t pitch, int64_t y0, int64_t rows) {
-  using S = Storage<T>;
-  const int64_t n = nx * rows;
-  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-       i < n; i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const int64_t y = y0 + i / nx, x = i % nx;
-    const int64_t o = y * pitch + x;
-    const bool solid = mask[o] == 1u;  // holds no fluid state: report rest
-    const float d = S::decode(static_cast<const T *>(f.d)[o]) * (1.0f / S::kD);
-    const float jx = S::decode(static_cast<const T *>(f.jx)[o]) * (1.0f / S::kJ);
-    const float jy = S::decode(static_cast<const T *>(f.jy)[o]) * (1.0f / S::kJ);
-    staging[i] = solid ? 1.0 : 1.0 + static_cast<double>(d);
-    staging[n + i] = solid ? 0.0 : static_cast<double>(jx);
-    staging[2 * n + i] = solid ? 0.0 : static_cast<double>(jy);
-  }
-}
-
-// Writes the solid-node storage values rho - 1 = 0, j = -F.
-template <typename T>
-__global__ void solid_storage_kernel(Fields f, const uint8_t *__restrict__ mask,
-                                     int64_t n, float fx, float fy) {
-  using S = Storage<T>;
-  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-       i < n; i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    if (mask[i] == 1u) {
-      static_cast<T *>(f.d)[i] = S::encode(0.0f);
-      static_cast<T *>(f.jx)[i] = S::encode(-fx * S::kJ);
-      static_cast<T *>(f.jy)[i] = S::encode(-fy * S::kJ);
-    }
-  }
-}
-
-// Tile variants: columns per lane, output rows per warp, resident blocks per
-// SM requested from the register allocator, shared-memory ring stages.
-struct Variant {
-  int cols, rows, min_blocks, stages;
-  bool dual;  // also carries the clean-tile code (flags per warp tile)
-};
-constexpr Variant kVariants[] = {
-    {4, 64, 2, 8, false}, {2, 64, 3, 12, false}, {4, 32, 2, 8, false},
-    {2, 64, 4, 10, false}, {4, 8, 2, 8, false},  {2, 8, 3, 12, false},
-    {4, 64, 2, 8, true}};
-constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
-
-// Calls f(std::integral_constant<int, v>) for a run-time variant index v
-// (variant 0 for an index out of range).
-template <int kV = 0, typename F>
-auto with_variant(int v, F &&f) {
-  if constexpr (kV + 1 < kNumVariants) {
-    if (v == kV) return f(std::integral_constant<int, kV>{});
-    return with_variant<kV + 1>(v, static_cast<F &&>(f));
-  } else {
-    if (v == kV) return f(std::integral_constant<int, kV>{});
-    return f(std::integral_constant<int, 0>{});
-  }
-}
-
-// A variant forced through LBMTAU1_STEP_VARIANT (tuning), or -1.
-int forced_variant() {
-  static int v = [] {
-    const char *e = getenv("LBMTAU1_STEP_VARIANT");
-    int i = e ? atoi(e) : -1;
-    return (i >= 0 && i < kNumVariants) ? i : -1;
-  }();
-  return v;
-}
-
-int active_variant() {
-  const int f = forced_variant();
-  return f >= 0 ? f : 0;
-}
-
-dim3 step_grid(int64_t nx, int64_t ny, int vi) {
-  const Variant v = kVariants[(vi >= 0 && vi < kNumVariants) ? vi : 0];
-  const int64_t tile_x = (kLanes - 2) * v.cols;
-  const int64_t tile_y = static_cast<int64_t>(kWarps) * v.rows;
-  const int64_t gx = (nx + tile_x - 1) / tile_x;
-  const int64_t gy = (ny + tile_y - 1) / tile_y;
-  return dim3(static_cast<unsigned>(gx), static_cast<unsigned>(gy), 1);
-}
-
-template <typename T, int kV, bool kReduce>
-cudaError_t launch_variant(const StepLaunch &a, dim3 g, cudaStream_t s) {
-  constexpr Variant v = kVariants[kV];
-  constexpr int smem = smem_bytes<T, v.cols, v.stages>();
-  static_assert(smem <= 227 * 1024, "shared memory per block");
-  auto kern =
-      lbm_step_kernel<T, v.cols, v.rows, v.min_blocks, v.stages, kReduce, v.dual>;
-  static cudaError_t attr = cudaFuncSetAttribute(
-      kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (attr != cudaSuccess) return attr;
-  (void)cudaGetLastError();  // an earlier, unrelated non-sticky error
-  kern<<<g, kThreads, smem, s>>>(a);
-  return cudaGetLastError();
-}
-
-template <typename T, bool kReduce>
-cudaError_t launch_any(const StepLaunch &a, dim3 g, cudaStream_t s) {
-  return with_variant(a.variant, [&](auto kv) {
-    return launch_variant<T, decltype(kv)::value, kReduce>(a, g, s);
-  });
-}
-
-// Resident blocks per SM of a variant's (unreduced) step kernel.
-template <typename T, int kV>
-int occupancy_of() {
-  constexpr Variant v = kVariants[kV];
-  constexpr int smem = smem_bytes<T, v.cols, v.stages>();
-  auto kern =
-      lbm_step_kernel<T, v.cols, v.rows, v.min_blocks, v.stages, false, v.dual>;
-  static int occ = [&] {
-    int n = 0;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             smem) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, kThreads,
-                                                      smem) != cudaSuccess)
-      n = 0;
-    return n;
-  }();
-  return occ;
-}
-
-template <typename T>
-int occupancy(int v) {
-  return with_variant(v, [](auto kv) {
-    return occupancy_of<T, decltype(kv)::value>();
-  });
-}
-
-// Picks the variant with the shortest expected step time for an nx x ny
-// domain.  The model, fitted to step times measured on a GB300 over the
-// 256^2 .. 16384^2 cavity sweep: blocks are spread evenly over the SMs, so the
-// busiest SM runs ceil(blocks / SMs) of them; one block marches kRows + 2
-// source rows per warp, each costing its columns per lane (two columns per
-// lane cost 1.215 times as much per column as four: fewer loads in flight per
-// instruction); and an SM that holds two or more blocks at once gets through
-// them 1.3 times as fast as one block alone (the kernel is issue-bound, so a
-// second block adds little and a third nothing measurable).
-template <typename T>
-int choose_variant_t(int64_t nx, int64_t ny) {
-  constexpr double kTwoColumnCost = 1.215;
-  constexpr double kSharedSpeedup = 1.3;
-  static int sms = [] {
-    int dev = 0, n = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) !=
-            cudaSuccess)
-      n = 0;
-    return n;
-  }();
-  if (sms <= 0) return 0;
-  int best = 0;
-  double best_time = 0.0;
-  for (int i = 0; i < kNumVariants; ++i) {
-    const Variant v = kVariants[i];
-    const int occ = occupancy<T>(i);
-    if (occ <= 0) continue;
-    const dim3 g = step_grid(nx, ny, i);
-    const int64_t blocks = static_cast<int64_t>(g.x) * g.y;
-    const int64_t per_sm = (blocks + sms - 1) / sms;
-    const double block_time =
-        (v.rows + 2.0) * v.cols * (v.cols == 2 ? kTwoColumnCost : 1.0);
-    const double rate = (occ >= 2 && per_sm >= 2) ? kSharedSpeedup : 1.0;
-    if (v.dual) continue;  // chosen only through dual_variant, by its flags
-    const double t = static_cast<double>(per_sm) * block_time / rate;
-    if (best_time == 0.0 || t < best_time * (1.0 - 1e-9)) {
-      best_time = t;
-      best = i;
-    }
-  }
-  return best;
-}
-
-template <typename T, int kV, bool kReduce>
-cudaError_t launch_batch_variant(const BatchLaunch &b, cudaStream_t s) {
-  constexpr Variant v = kVariants[kV];
-  constexpr int smem = smem_bytes<T, v.cols, v.stages>();
-  auto kern =
-      lbm_batch_kernel<T, v.cols, v.rows, v.min_blocks, v.stages, kReduce,
-                       v.dual>;
-  // persistent grid: every resident block slot of the device, computed once
-  static int grid = [&] {
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             smem) != cudaSuccess)
-      return 0;
-    int dev = 0, sms = 0, per_sm = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
-            cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads,
-                                                      smem) != cudaSuccess)
-      return 0;
-    return sms * (per_sm > 0 ? per_sm : 1);
-  }();
-  if (grid <= 0) return cudaErrorInvalidConfiguration;
-  (void)cudaGetLastError();
-  kern<<<grid, kThreads, smem, s>>>(b);
-  return cudaGetLastError();
-}
-
-template <typename T, bool kReduce>
-cudaError_t launch_batch_any(int v, const BatchLaunch &b, cudaStream_t s) {
-  return with_variant(v, [&](auto kv) {
-    return launch_batch_variant<T, decltype(kv)::value, kReduce>(b, s);
-  });
-}
-
-template <typename T>
-cudaError_t launch_step_t(const StepLaunch &a, bool reduce, cudaStream_t s) {
-  const dim3 g = step_grid(a.nx, a.ny, a.variant);
-  return reduce ? launch_any<T, true>(a, g, s) : launch_any<T, false>(a, g, s);
-}
-
-template <typename T>
-cudaError_t launch_batch_t(int v, const BatchLaunch &b, bool reduce,
-                           cudaStream_t s) {
-  return reduce ? launch_batch_any<T, true>(v, b, s)
-                : launch_batch_any<T, false>(v, b, s);
 }
 
 }  // namespace
+
 
 int64_t step_blocks(int64_t nx, int64_t ny) {
   // the largest grid over all variants, so a workspace fits any of them
@@ -1362,11 +146,7 @@ int default_variant() { return active_variant(); }
 cudaError_t launch_batch(int v, const BatchLaunch &b, bool reduce,
                          cudaStream_t s) {
   if (v < 0 || v >= kNumVariants) return cudaErrorInvalidValue;
-  switch (b.storage) {
-    case kStorageF16: return launch_batch_t<__half>(v, b, reduce, s);
-    case kStorageBF16: return launch_batch_t<__nv_bfloat16>(v, b, reduce, s);
-    default: return launch_batch_t<float>(v, b, reduce, s);
-  }
+  return ops(b.storage).batch(v, b, reduce, s);
 }
 
 cudaError_t launch_batch_finalize(const BatchMember *members, int nmembers,
@@ -1421,21 +201,13 @@ int dual_variant(int v, int64_t nx, int64_t ny) {
 int choose_variant(int64_t nx, int64_t ny, int storage) {
   const int f = forced_variant();
   if (f >= 0) return f;
-  switch (storage) {
-    case kStorageF16: return choose_variant_t<__half>(nx, ny);
-    case kStorageBF16: return choose_variant_t<__nv_bfloat16>(nx, ny);
-    default: return choose_variant_t<float>(nx, ny);
-  }
+  return ops(storage).choose(nx, ny);
 }
 
 cudaError_t launch_step(const StepLaunch &a, bool reduce, cudaStream_t s) {
   if (a.ny >= (int64_t(1) << 30) || a.nx >= (int64_t(1) << 30))
     return cudaErrorInvalidValue;  // the tile loop indexes rows in 32 bits
-  switch (a.storage) {
-    case kStorageF16: return launch_step_t<__half>(a, reduce, s);
-    case kStorageBF16: return launch_step_t<__nv_bfloat16>(a, reduce, s);
-    default: return launch_step_t<float>(a, reduce, s);
-  }
+  return ops(a.storage).step(a, reduce, s);
 }
 
 cudaError_t launch_tile_flags(int v, const uint8_t *mask, int64_t nx,
@@ -1463,69 +235,23 @@ cudaError_t launch_finalize(const double *partials, int64_t nblocks,
   return cudaGetLastError();
 }
 
-namespace {
-int copy_grid(int64_t n) {
-  const int64_t b = (n + 255) / 256;
-  return static_cast<int>(b < 4096 ? (b < 1 ? 1 : b) : 4096);
-}
-
-template <typename T>
-cudaError_t pack_t(const double *staging, Fields f, int64_t nx, int64_t pitch,
-                   int64_t y0, int64_t rows, cudaStream_t s) {
-  (void)cudaGetLastError();
-  pack_kernel<T><<<copy_grid(nx * rows), 256, 0, s>>>(staging, f, nx, pitch,
-                                                      y0, rows);
-  return cudaGetLastError();
-}
-template <typename T>
-cudaError_t unpack_t(Fields f, const uint8_t *mask, double *staging,
-                     int64_t nx, int64_t pitch, int64_t y0, int64_t rows,
-                     cudaStream_t s) {
-  (void)cudaGetLastError();
-  unpack_kernel<T><<<copy_grid(nx * rows), 256, 0, s>>>(f, mask, staging, nx,
-                                                        pitch, y0, rows);
-  return cudaGetLastError();
-}
-template <typename T>
-cudaError_t solid_t(Fields f, const uint8_t *mask, int64_t n, float fx,
-                    float fy, cudaStream_t s) {
-  (void)cudaGetLastError();
-  solid_storage_kernel<T><<<copy_grid(n), 256, 0, s>>>(f, mask, n, fx, fy);
-  return cudaGetLastError();
-}
-}  // namespace
 
 cudaError_t launch_pack(int storage, const double *staging, Fields f,
                         int64_t nx, int64_t pitch, int64_t y0, int64_t rows,
                         cudaStream_t s) {
-  switch (storage) {
-    case kStorageF16: return pack_t<__half>(staging, f, nx, pitch, y0, rows, s);
-    case kStorageBF16:
-      return pack_t<__nv_bfloat16>(staging, f, nx, pitch, y0, rows, s);
-    default: return pack_t<float>(staging, f, nx, pitch, y0, rows, s);
-  }
+  return ops(storage).pack(staging, f, nx, pitch, y0, rows, s);
 }
 
 cudaError_t launch_unpack(int storage, Fields f, const uint8_t *mask,
                           double *staging, int64_t nx, int64_t pitch,
                           int64_t y0, int64_t rows, cudaStream_t s) {
-  switch (storage) {
-    case kStorageF16:
-      return unpack_t<__half>(f, mask, staging, nx, pitch, y0, rows, s);
-    case kStorageBF16:
-      return unpack_t<__nv_bfloat16>(f, mask, staging, nx, pitch, y0, rows, s);
-    default: return unpack_t<float>(f, mask, staging, nx, pitch, y0, rows, s);
-  }
+  return ops(storage).unpack(f, mask, staging, nx, pitch, y0, rows, s);
 }
 
 cudaError_t launch_solid_storage(int storage, Fields f, const uint8_t *mask,
                                  int64_t n, float fx, float fy,
                                  cudaStream_t s) {
-  switch (storage) {
-    case kStorageF16: return solid_t<__half>(f, mask, n, fx, fy, s);
-    case kStorageBF16: return solid_t<__nv_bfloat16>(f, mask, n, fx, fy, s);
-    default: return solid_t<float>(f, mask, n, fx, fy, s);
-  }
+  return ops(storage).solid(f, mask, n, fx, fy, s);
 }
 
 int storage_bytes(int storage) {

@@ -35,11 +35,15 @@ struct StepLaunch {
   unsigned int *flag;   // sticky instability flag (reduced steps only)
   int storage = kStorageF32;
   int variant = 0;      // tile variant (see choose_variant)
-  int sr = 0;           // 16-bit storage: stochastic rounding
+  int sr = 0;           // stochastic rounding (16-bit: all fields; FP32: j)
   uint32_t step = 0;    // the domain's step count (seeds the rounding)
   // one byte per warp tile of this launch's tile variant: 1 when the tile
   // is clean (launch_tile_flags); null: every tile takes the general code
   const uint8_t *clean = nullptr;
+  // how long a warp waits for a staged row before it gives up (raising
+  // kFlagCopyTimeout); 0 gives up at once.  Draining the copies still in
+  // flight before a warp leaves its tile always keeps the one-second bound.
+  unsigned long long wait_ns = 1000000000ull;
 };
 
 // One member of a batch (see launch_batch): both field copies, the copy that
@@ -57,7 +61,7 @@ struct BatchMember {
   int64_t gx;        // block tiles along x for the batch's tile variant
   int64_t nblocks;   // block tiles of the member
   int cur;           // copy holding the state when the batch step starts
-  int sr;            // 16-bit storage: stochastic rounding
+  int sr;            // stochastic rounding (as StepLaunch::sr)
   int64_t step_base; // member's step count minus the batch clock
   const uint8_t *clean;  // clean-tile flags for the batch's variant
 };
@@ -72,6 +76,26 @@ struct BatchLaunch {
   unsigned int *clock;    // batch steps taken (advanced by each launch)
   unsigned int *done;     // blocks finished in this launch (zero between)
 };
+
+// The launchers of one storage format.  The kernels are templates on the
+// storage type, instantiated once per format in its own translation unit
+// (lbm_step_f32.cu, lbm_step_f16.cu, lbm_step_bf16.cu); the entry points
+// below dispatch on the format through these tables.
+struct StorageOps {
+  cudaError_t (*step)(const StepLaunch &a, bool reduce, cudaStream_t s);
+  cudaError_t (*batch)(int v, const BatchLaunch &b, bool reduce,
+                       cudaStream_t s);
+  int (*choose)(int64_t nx, int64_t ny);
+  cudaError_t (*pack)(const double *staging, Fields f, int64_t nx,
+                      int64_t pitch, int64_t y0, int64_t rows,
+                      cudaStream_t s);
+  cudaError_t (*unpack)(Fields f, const uint8_t *mask, double *staging,
+                        int64_t nx, int64_t pitch, int64_t y0, int64_t rows,
+                        cudaStream_t s);
+  cudaError_t (*solid)(Fields f, const uint8_t *mask, int64_t n, float fx,
+                       float fy, cudaStream_t s);
+};
+extern const StorageOps kOpsF32, kOpsF16, kOpsBF16;
 
 // Tile variants: their number, the block tile size of variant v, and the
 // default variant of the single-domain path.
