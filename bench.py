@@ -61,7 +61,6 @@ def parse_args(argv=None):
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--batched-domains", type=int, default=512)
     ap.add_argument("--batched-steps", type=int, default=2000)
-    ap.add_argument("--batched-plain-steps", type=int, default=200)
     ap.add_argument("--porous-cap", type=int, default=50000,
                     help="step cap of the porous run to residual 1e-8")
     ap.add_argument("--serving-requests", type=int, default=32)
@@ -452,7 +451,7 @@ def run_porous(binding, stream, n=4096, tol=1e-8, cap=50000, check=2000):
     return out
 
 
-def run_batched(binding, domains, steps, plain_steps=200, storage="f32"):
+def run_batched(binding, domains, steps, storage="f32"):
     """Configuration: 512 independent domains (seeded thirds of channels,
     cavities and porous samples, sides log-uniform in [64, 1024]), 2000 steps
     each, in one storage format; batched (one launch per step for all
@@ -483,17 +482,16 @@ def run_batched(binding, domains, steps, plain_steps=200, storage="f32"):
     for d in doms:
         d.close()
     torch.cuda.empty_cache()
-    # the plain form, one domain after another, timed over plain_steps of the
-    # steps (its time per step does not depend on the step) and scaled
+    # the plain form, one domain after another, every one of its steps timed
     doms = [binding.Domain.from_problem(p, stream=stream, storage=storage)
             for p in probs]
     stream.synchronize()
     e0.record(stream)
     for d in doms:
-        d.step(plain_steps)
+        d.step(steps)
     e1.record(stream)
     stream.synchronize()
-    t_plain = e0.elapsed_time(e1) / 1e3 * steps / plain_steps
+    t_plain = e0.elapsed_time(e1) / 1e3
     for d in doms:
         d.close()
     torch.cuda.empty_cache()
@@ -503,7 +501,7 @@ def run_batched(binding, domains, steps, plain_steps=200, storage="f32"):
             "nodes": int(nodes), "variant": chosen,
             "autotune_ms_per_step": [round(t, 4) for t in tuned],
             "batched_s": round(t_batch, 4), "plain_s": round(t_plain, 4),
-            "plain_timed_steps": plain_steps,
+            "plain_timed_steps": steps,
             "solves_per_s_batched": round(domains / t_batch, 2),
             "solves_per_s_plain": round(domains / t_plain, 2),
             "mlups_batched": round(nodes * steps / t_batch / 1e6, 1),
@@ -724,11 +722,9 @@ def main(argv=None):
         line["precision"] = run_precision(binding, stream)
     if rank == 0 and not args.no_batched:
         line["batched"] = run_batched(binding, args.batched_domains,
-                                      args.batched_steps,
-                                      plain_steps=args.batched_plain_steps)
+                                      args.batched_steps)
         line["batched_f16"] = run_batched(
-            binding, args.batched_domains, args.batched_steps,
-            plain_steps=max(1, args.batched_plain_steps // 2), storage="f16")
+            binding, args.batched_domains, args.batched_steps, storage="f16")
     if rank == 0 and not args.no_serving:
         line["serving"] = run_serving(args.serving_requests)
     if rank == 0 and not args.no_cpu_baseline:

@@ -59,7 +59,7 @@ def test_workspace_follows_storage_model(b):
 
 
 @pytest.mark.parametrize("bad", [dict(nx=0), dict(ny=0), dict(nx=-3),
-                                 dict(storage=7), dict(rounding=2), dict(rounding=-1),
+                                 dict(storage=7), dict(rounding=3), dict(rounding=-1),
                                  dict(fx=float("nan"))])
 def test_invalid_params(b, bad):
     p = b.make_params(10, 10)
@@ -114,6 +114,12 @@ def test_call_order_and_arguments_checked_on_host(b):
             assert lib.lbm_set_variant(ctx, v) == b.LBM_OK
             assert b.lbm_variant(ctx) == v
         assert lib.lbm_set_variant(ctx, -1) == b.LBM_OK
+        # the staged-row wait limit: 0 .. 1 s
+        assert lib.lbm_set_copy_wait_ns(ctx, -1) == b.LBM_E_INVAL
+        assert lib.lbm_set_copy_wait_ns(ctx, 10**9 + 1) == b.LBM_E_INVAL
+        assert lib.lbm_set_copy_wait_ns(ctx, 0) == b.LBM_OK
+        assert lib.lbm_set_copy_wait_ns(ctx, 10**9) == b.LBM_OK
+        assert lib.lbm_set_copy_wait_ns(None, 0) == b.LBM_E_INVAL
         # the step count that seeds stochastic rounding
         assert b.lbm_step_count(ctx) == 0
         b.lbm_set_step_count(ctx, 12345)

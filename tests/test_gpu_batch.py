@@ -183,3 +183,53 @@ def test_batch_member_matches_oracle(b):
         for a_, b_ in zip(g, o):
             assert np.abs(a_ - b_)[fluid].max() <= 2e-6 * amp * np.sqrt(20) + 1e-9
     batch.close()
+
+
+def velocity_error(a, b):
+    ua = np.stack([a[1] / a[0], a[2] / a[0]])
+    ub = np.stack([b[1] / b[0], b[2] / b[0]])
+    return np.abs(ua - ub).max() / np.abs(ub).max()
+
+
+def test_batch_mix512_sample_matches_oracle(b):
+    """The batched configuration itself: all 512 domains of the seeded mix
+    (channel / cavity / porous thirds, sides log-uniform in [64, 1024]) in
+    one batch with the autotuner's tile variant, 2000 steps, FP32 storage
+    with stochastic rounding of the momentum; a seeded sample of 16 members
+    (the largest of each kind among them included) is compared node by node
+    with the oracle's 2000 steps, at the 1e-5 velocity bound.  (Rounded to
+    nearest, FP32 storage alone drifts past that bound on the slowly
+    accelerating channels of the mix: tests/test_fp32_storage_floor.py.)"""
+    import torch
+    oracle.set_threads(oracle.max_threads())
+    probs = wl.batch_mix(512, seed=0)
+    rng = np.random.default_rng(512)
+    pick = set(int(i) for i in rng.choice(len(probs), 13, replace=False))
+    for k in range(3):   # the largest domain of each kind
+        same = [i for i in range(len(probs)) if i % 3 == k]
+        pick.add(max(same, key=lambda i: probs[i].mask.size))
+    pick = sorted(pick)[:16]
+    stream = torch.cuda.Stream()
+    doms = [b.Domain.from_problem(p, stream=stream, rounding="stochastic")
+            for p in probs]
+    tiles = sum(b.lbm_tile_count(p.mask.shape[1], p.mask.shape[0])
+                for p in probs)
+    batch = b.Batch(len(doms), tiles, stream=stream)
+    for d in doms:
+        batch.add(d)
+    batch.autotune(2)          # real steps: the members start again below
+    for d, p in zip(doms, probs):
+        d.set_moments(p.rho, p.jx, p.jy)
+    batch.step(2000)
+    res, _, status = batch.residuals()
+    assert all(s == b.LBM_OK for s in status[: len(doms)])
+    for i in pick:
+        p = probs[i]
+        g = doms[i].moments()
+        o = oracle.run(p.mask, *p.state(), 2000, p.periodic, p.force)
+        err = velocity_error(g, o)
+        assert err <= 1e-5, (i, p.name, p.mask.shape, err)
+        assert np.abs(g[0] - o[0]).max() <= 1e-5, (i, p.name)
+    batch.close()
+    for d in doms:
+        d.close()

@@ -52,10 +52,16 @@ def velocity_error(a, b):
     return np.abs(ua - ub).max() / np.abs(ub).max()
 
 
-def test_channel_64x32_5000_steps(binding):
-    """Poiseuille channel, 64 x 32, 5000 steps, u_max ~ 0.01."""
+@pytest.mark.parametrize("rounding", ["nearest", "stochastic"])
+def test_channel_64x32_5000_steps(binding, rounding):
+    """Poiseuille channel, 64 x 32, 5000 steps, u_max ~ 0.01, FP32 storage
+    rounded to nearest (the default) and stochastically."""
     p = wl.channel(64, 32, 0.01)
-    g, (res, mass) = run_gpu(binding, p, 5000)
+    d = binding.Domain.from_problem(p, rounding=rounding)
+    d.step(5000)
+    g = d.moments()
+    res, mass = d.residual()
+    d.close()
     o = oracle.run(p.mask, *p.state(), 5000, p.periodic, p.force)
     err = velocity_error(g, o)
     assert err <= 1e-5, err
@@ -229,52 +235,45 @@ def sample_nodes(shape, count, seed=0):
 
 
 def test_cavity_1024_full_size(binding):
-    """Lid-driven cavity 1024^2, lid u = 0.1: every node against the oracle
-    after 2000 steps; then the 20000-step run of the bench configuration,
-    checked for stability, a shrinking residual, and one more step on 20000
-    sampled nodes against the oracle's single-node update."""
+    """Lid-driven cavity 1024^2, lid u = 0.1 (Section 3's cavity, Re = 614):
+    every node against the oracle after the configuration's full 20000 steps,
+    at the bound the method is held to, max|u_gpu - u_oracle| / max|u_oracle|
+    <= 1e-5; on the way, the residual of every 2000-step call shrinks."""
     oracle.set_threads(oracle.max_threads())
     p = wl.cavity(1024, 0.1)
     d = binding.Domain.from_problem(p)
-    d.step(2000)
-    g = d.moments()
-    o = oracle.run(p.mask, *p.state(), 2000, p.periodic, p.force)
-    assert velocity_error(g, o) <= 1e-5
-    assert np.abs(g[0] - o[0]).max() <= 1e-6
     res_prev = None
-    for _ in range(9):
+    for _ in range(10):
         d.step(2000)
         res, _ = d.residual()
         assert np.isfinite(res)
         if res_prev is not None:
             assert res < res_prev
         res_prev = res
-    d.step(1999)
-    before = d.moments()
-    d.step(1)
-    after = d.moments()
-    nodes = sample_nodes(p.mask.shape, 20000)
-    ref = oracle.step_nodes(p.mask, *before, nodes, p.periodic, p.force)
-    for f in range(3):
-        got = after[f].ravel()[nodes]
-        assert np.abs(got - ref[:, f]).max() <= tolerance(0.1, 1)
+    g = d.moments()
     d.close()
+    o = oracle.run(p.mask, *p.state(), 20000, p.periodic, p.force)
+    assert velocity_error(g, o) <= 1e-5
+    assert np.abs(g[0] - o[0]).max() <= 1e-5
 
 
 def test_porous_4096_full_size(binding):
     """Periodic porous medium 4096^2 (seeded discs, solid fraction 0.30,
-    f_x = 1e-5): every node against the oracle after 20 steps, then a
-    single-step sampled check after 2000 steps, and the Reynolds number of the
+    f_x = 1e-5): every node against the oracle after 2000 steps at the
+    1e-5 velocity bound; then on to 50000 steps (near the FP32 residual floor
+    of this flow), where one more step is checked on 20000 sampled nodes
+    against the oracle's single-node update, and the Reynolds number of the
     flow stays below 1."""
     oracle.set_threads(oracle.max_threads())
     p = wl.porous(4096, seed=0)
     d = binding.Domain.from_problem(p)
-    d.step(20)
+    d.step(2000)
     g = d.moments()
-    o = oracle.run(p.mask, *p.state(), 20, p.periodic, p.force)
-    for a, b in zip(g, o):
-        assert np.abs(a - b).max() <= tolerance(1e-3, 20)
-    d.step(1979)
+    o = oracle.run(p.mask, *p.state(), 2000, p.periodic, p.force)
+    assert velocity_error(g, o) <= 1e-5
+    assert np.abs(g[0] - o[0]).max() <= 1e-6
+    del g, o
+    d.step(47999)
     before = d.moments()
     d.step(1)
     after = d.moments()
@@ -406,6 +405,36 @@ def test_unstable_state_is_reported(binding):
         res, mass = d.residual()
         assert np.isfinite(res), name
         d.close()
+
+
+def test_copy_wait_timeout_is_reported(binding):
+    """Failure detection without a fault: with a zero wait limit every wait
+    of the step kernel for a staged row gives up at once; each warp then lets
+    its copies in flight land (that drain keeps its one-second bound), raises
+    the copy-timeout flag and stops.  lbm_residual reports LBM_E_CUDA with the
+    timeout message, on a capturable stream (graph chunks) and on the default
+    one; with the limit restored and the state loaded again, stepping gives
+    the oracle's result."""
+    import torch
+    p = wl.random_problem(300, 170, seed=31, amp=0.02, periodic=(True, False))
+    for stream in (None, torch.cuda.Stream()):
+        d = binding.Domain.from_problem(p, stream=stream)
+        d.step(40)          # graphs captured with the default limit
+        d.set_copy_wait_ns(0)
+        d.step(40)
+        with pytest.raises(binding.LbmError, match="wait limit") as e:
+            d.residual()
+        assert e.value.status == binding.LBM_E_CUDA
+        d.set_copy_wait_ns(10**9)
+        d.set_moments(p.rho, p.jx, p.jy)
+        d.step(20)
+        res, mass = d.residual()
+        assert np.isfinite(res)
+        g = d.moments()
+        d.close()
+        o = oracle.run(p.mask, *p.state(), 20, p.periodic, p.force)
+        for a, b in zip(g, o):
+            assert np.abs(a - b).max() <= tolerance(0.02, 20)
 
 
 def test_residual_matches_oracle(binding):
