@@ -57,6 +57,11 @@ def _load():
     lib.oracle_step_nodes.argtypes = ([i64, i64, i32, i32, f64, f64]
                                       + [vp] * 5 + [i64, vp])
     lib.oracle_residual.argtypes = [i64] + [vp] * 9
+    lib.oracle_step_sc.argtypes = [i64, i64, i32, i32, f64, f64, f64] + [vp] * 7
+    lib.oracle_run_sc.argtypes = ([i64, i64, i32, i32, f64, f64, f64]
+                                  + [vp] * 4 + [i64])
+    lib.oracle_run_sc.restype = ctypes.c_int
+    lib.oracle_sc_force.argtypes = [i64, i64, i32, i32, f64] + [vp] * 4
     lib.oracle_set_threads.argtypes = [i32]
     lib.oracle_max_threads.restype = i32
     _lib = lib
@@ -142,3 +147,45 @@ def residual(mask, old, new):
                         *[_p(x) for x in b], ctypes.byref(res),
                         ctypes.byref(mass))
     return res.value, mass.value
+
+
+def step_sc(mask, R, U, V, g, periodic=(True, True), force=(0.0, 0.0)):
+    """One Shan-Chen multiphase step with coupling ``g`` (Section 4,
+    Eq. f_sc; see lbm_oracle.c for the readings); returns new (R, U, V)."""
+    lib = _load()
+    mask = np.ascontiguousarray(mask, dtype=np.uint8)
+    ny, nx = mask.shape
+    R, U, V = _f64(R), _f64(U), _f64(V)
+    out = [np.empty_like(R) for _ in range(3)]
+    lib.oracle_step_sc(nx, ny, int(periodic[0]), int(periodic[1]),
+                       float(force[0]), float(force[1]), float(g), _p(mask),
+                       _p(R), _p(U), _p(V), _p(out[0]), _p(out[1]),
+                       _p(out[2]))
+    return tuple(out)
+
+
+def run_sc(mask, R, U, V, nsteps, g, periodic=(True, True),
+           force=(0.0, 0.0)):
+    """``nsteps`` multiphase steps from (R, U, V); returns new (R, U, V)."""
+    lib = _load()
+    mask = np.ascontiguousarray(mask, dtype=np.uint8)
+    ny, nx = mask.shape
+    R, U, V = _f64(R).copy(), _f64(U).copy(), _f64(V).copy()
+    rc = lib.oracle_run_sc(nx, ny, int(periodic[0]), int(periodic[1]),
+                           float(force[0]), float(force[1]), float(g),
+                           _p(mask), _p(R), _p(U), _p(V), int(nsteps))
+    if rc != 0:
+        raise MemoryError("oracle_run_sc could not allocate its scratch grid")
+    return R, U, V
+
+
+def sc_force(mask, R, g, periodic=(True, True)):
+    """The Shan-Chen force (FX, FY) of every non-solid node."""
+    lib = _load()
+    mask = np.ascontiguousarray(mask, dtype=np.uint8)
+    ny, nx = mask.shape
+    R = _f64(R)
+    FX, FY = np.empty_like(R), np.empty_like(R)
+    lib.oracle_sc_force(nx, ny, int(periodic[0]), int(periodic[1]), float(g),
+                        _p(mask), _p(R), _p(FX), _p(FY))
+    return FX, FY

@@ -194,6 +194,140 @@ void oracle_step_nodes(int64_t nx, int64_t ny, int32_t periodic_x,
   }
 }
 
+/* ---- Shan-Chen multiphase step (Section 4, Eq. f_sc) ----
+ *
+ * Section 4 adds the pseudo-potential interaction force
+ *   F_SC(x) = psi(x) sum_i alpha_i psi(x + e_i) G(e_i)        (Eq. f_sc)
+ * to the step: with tau = 1 the populations leaving a node are the
+ * equilibria of its density and of its velocity shifted by the force, so
+ * F_SC enters exactly where Algorithm 1 adds the body force, before the
+ * division by the density.  (Kupershtokh's exact-difference forcing, which
+ * the paper's performance test uses, adds f^eq(rho, u + F / rho) -
+ * f^eq(rho, u) to the collision; at tau = 1 that is the same shift.)
+ * The paper leaves psi, alpha_i and G(e_i) to the model of Shan and Chen;
+ * the readings taken here are that model's own:
+ *   psi(rho) = 1 - exp(-rho),  alpha_i = w_i,  G(e_i) = -g e_i,
+ * so F_SC(x) = -g psi(x) sum_i w_i psi(x + e_i) e_i, with a scalar coupling
+ * g (g < -4 separates phases).  A solid node, or a point outside a
+ * non-periodic edge, has psi = 0.  The rest of the step is Algorithm 1 as in
+ * update_node above; the force on every pulled neighbour needs the
+ * potentials of that neighbour's own neighbours, the two-fold loop that
+ * Section 3 names. */
+
+/* psi of flat index p (-1: outside a non-periodic edge). */
+static double sc_psi(const domain *d, const double *R, int64_t p) {
+  if (p < 0 || d->mask[p] == NODE_SOLID) return 0.0;
+  return 1.0 - exp(-R[p]);
+}
+
+/* Eq. (f_sc) at node (x, y): the inner loop over its neighbours. */
+static void sc_force(const domain *d, double g, const double *R, int64_t x,
+                     int64_t y, double *fsx, double *fsy) {
+  double sx = 0.0, sy = 0.0;
+  for (int i = 0; i < 9; ++i) {
+    const double ps = sc_psi(d, R, neighbour_index(d, x + ex[i], y + ey[i]));
+    sx += omega[i] * ps * ex[i];
+    sy += omega[i] * ps * ey[i];
+  }
+  const double own = sc_psi(d, R, y * d->nx + x);
+  *fsx = -g * own * sx;
+  *fsy = -g * own * sy;
+}
+
+/* One node of the multiphase step: as update_node, with F_SC of each pulled
+ * neighbour added to its momentum beside the body force. */
+static void update_node_sc(const domain *d, double g, const double *R,
+                           const double *U, const double *V, int64_t x,
+                           int64_t y, double *r_out, double *u_out,
+                           double *v_out) {
+  const int64_t i = y * d->nx + x;
+  if (d->mask[i] != NODE_FLUID) {
+    *r_out = R[i];
+    *u_out = U[i];
+    *v_out = V[i];
+    return;
+  }
+  double r_new = 0.0, u_new = 0.0, v_new = 0.0;
+  for (int k = 0; k < 9; ++k) {
+    const int ik = inv_dir[k];
+    const int64_t px = x + ex[k], py = y + ey[k];
+    const int64_t p = neighbour_index(d, px, py);
+    double feq;
+    if (p >= 0 && d->mask[p] != NODE_SOLID) {
+      double fsx, fsy;
+      sc_force(d, g, R, p % d->nx, p / d->nx, &fsx, &fsy);
+      const double r = R[p];
+      const double u = (U[p] + d->fx + fsx) / r;
+      const double v = (V[p] + d->fy + fsy) / r;
+      const double eu = ex[ik] * u + ey[ik] * v;
+      feq = omega[ik] * r *
+            (1.0 - 1.5 * (u * u + v * v) + 3.0 * eu + 4.5 * eu * eu);
+    } else {
+      feq = omega[k] * R[i];
+    }
+    r_new += feq;
+    u_new += ex[ik] * feq;
+    v_new += ey[ik] * feq;
+  }
+  *r_out = r_new;
+  *u_out = u_new;
+  *v_out = v_new;
+}
+
+/* One multiphase time step with coupling g: reads (R0, U0, V0), writes
+ * (R1, U1, V1). */
+void oracle_step_sc(int64_t nx, int64_t ny, int32_t periodic_x,
+                    int32_t periodic_y, double fx, double fy, double g,
+                    const uint8_t *mask, const double *R0, const double *U0,
+                    const double *V0, double *R1, double *U1, double *V1) {
+  const domain d = make_domain(nx, ny, periodic_x, periodic_y, fx, fy, mask);
+#pragma omp parallel for schedule(static)
+  for (int64_t y = 0; y < ny; ++y)
+    for (int64_t x = 0; x < nx; ++x) {
+      const int64_t i = y * nx + x;
+      update_node_sc(&d, g, R0, U0, V0, x, y, &R1[i], &U1[i], &V1[i]);
+    }
+}
+
+/* nsteps multiphase steps in place on (R, U, V); 0, or -1 without memory. */
+int oracle_run_sc(int64_t nx, int64_t ny, int32_t periodic_x,
+                  int32_t periodic_y, double fx, double fy, double g,
+                  const uint8_t *mask, double *R, double *U, double *V,
+                  int64_t nsteps) {
+  const size_t n = (size_t)nx * (size_t)ny;
+  double *tmp = (double *)malloc(3 * n * sizeof(double));
+  if (!tmp) return -1;
+  double *src[3] = {R, U, V};
+  double *dst[3] = {tmp, tmp + n, tmp + 2 * n};
+  for (int64_t s = 0; s < nsteps; ++s) {
+    oracle_step_sc(nx, ny, periodic_x, periodic_y, fx, fy, g, mask, src[0],
+                   src[1], src[2], dst[0], dst[1], dst[2]);
+    for (int f = 0; f < 3; ++f) {
+      double *t = src[f];
+      src[f] = dst[f];
+      dst[f] = t;
+    }
+  }
+  if (src[0] != R)
+    for (int f = 0; f < 3; ++f) memcpy(dst[f], src[f], n * sizeof(double));
+  free(tmp);
+  return 0;
+}
+
+/* The multiphase force F_SC of every node (0 at nodes that are not fluid or
+ * fixed), for tests of its sum and symmetry. */
+void oracle_sc_force(int64_t nx, int64_t ny, int32_t periodic_x,
+                     int32_t periodic_y, double g, const uint8_t *mask,
+                     const double *R, double *FX, double *FY) {
+  const domain d = make_domain(nx, ny, periodic_x, periodic_y, 0.0, 0.0, mask);
+  for (int64_t y = 0; y < ny; ++y)
+    for (int64_t x = 0; x < nx; ++x) {
+      const int64_t i = y * nx + x;
+      FX[i] = FY[i] = 0.0;
+      if (mask[i] != NODE_SOLID) sc_force(&d, g, R, x, y, &FX[i], &FY[i]);
+    }
+}
+
 /* Steady-state measures over fluid nodes (type 0), velocity u = (U, V) / R:
  *   residual = sqrt(sum |u_new - u_old|^2 / sum |u_new|^2)  (Section 3 uses
  *   the relative velocity change between consecutive steps; here it is taken

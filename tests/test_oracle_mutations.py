@@ -97,3 +97,72 @@ def test_mutation_is_caught(tmp_path, name):
     old, new = MUTATIONS[name]
     run = build_mutant(tmp_path, name, old, new)
     assert not checks_pass(run), name
+
+
+# Mistakes planted in the multiphase (Shan-Chen) step; the check is the
+# independent full-population code with the force from array shifts.
+SC_MUTATIONS = {
+    "coupling sign flipped": ("*fsx = -g * own * sx;", "*fsx = g * own * sx;"),
+    "own potential dropped": ("*fsy = -g * own * sy;", "*fsy = -g * sy;"),
+    "potential of a wall not zero":
+        ("if (p < 0 || d->mask[p] == NODE_SOLID) return 0.0;",
+         "if (p < 0) return 0.0;"),
+    "force taken at the receiving node":
+        ("sc_force(d, g, R, p % d->nx, p / d->nx, &fsx, &fsy);",
+         "sc_force(d, g, R, x, y, &fsx, &fsy);"),
+    "axis weights on the diagonals":
+        ("sx += omega[i] * ps * ex[i];", "sx += omega[1] * ps * ex[i];"),
+    "force dropped from the density division":
+        ("(U[p] + d->fx + fsx) / r", "(U[p] + d->fx) / r + fsx"),
+}
+
+
+def build_sc_mutant(tmp_path, old, new):
+    text = open(SRC).read()
+    assert old in text, old
+    path = tmp_path / "mutant_sc.c"
+    path.write_text(text.replace(old, new, 1))
+    lib = tmp_path / "mutant_sc.so"
+    subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c11",
+                           str(path), "-o", str(lib), "-lm"])
+    so = ctypes.CDLL(str(lib))
+    i64, i32, f64, vp = ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_void_p
+    so.oracle_run_sc.argtypes = [i64, i64, i32, i32, f64, f64, f64] + [vp] * 4 + [i64]
+    so.oracle_run_sc.restype = ctypes.c_int
+
+    def run(mask, R, U, V, n, g, periodic, force):
+        mask = np.ascontiguousarray(mask, np.uint8)
+        R, U, V = (np.array(a, np.float64) for a in (R, U, V))
+        ny, nx = mask.shape
+        so.oracle_run_sc(nx, ny, int(periodic[0]), int(periodic[1]), force[0],
+                         force[1], g, mask.ctypes.data, R.ctypes.data,
+                         U.ctypes.data, V.ctypes.data, n)
+        return R, U, V
+    return run
+
+
+def sc_checks_pass(run):
+    rng = np.random.default_rng(11)
+    for nx, ny, per, ps in [(7, 6, (True, True), 0.15), (6, 7, (False, True), 0.1)]:
+        mask = (rng.random((ny, nx)) < ps).astype(np.uint8)
+        R = rng.uniform(0.3, 2.0, (ny, nx))
+        U = 0.02 * rng.standard_normal((ny, nx))
+        V = 0.02 * rng.standard_normal((ny, nx))
+        R[mask == 1], U[mask == 1], V[mask == 1] = 1.0, 0.0, 0.0
+        a = run(mask, R, U, V, 6, -5.0, per, (1e-3, -1e-3))
+        b = fullpop_bgk.run_sc(mask, R, U, V, 6, -5.0, per, (1e-3, -1e-3))
+        if max(np.abs(x - y).max() for x, y in zip(a, b)) > 1e-13:
+            return False
+    return True
+
+
+def test_unmutated_sc_source_passes(tmp_path):
+    run = build_sc_mutant(tmp_path, "#include <math.h>", "#include <math.h>")
+    assert sc_checks_pass(run)
+
+
+@pytest.mark.parametrize("name", sorted(SC_MUTATIONS))
+def test_sc_mutation_is_caught(tmp_path, name):
+    old, new = SC_MUTATIONS[name]
+    run = build_sc_mutant(tmp_path, old, new)
+    assert not sc_checks_pass(run), name
