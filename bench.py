@@ -42,9 +42,11 @@ sys.path.insert(0, ROOT)
 
 METRIC = "D2Q9 LBMTau1 MLUPS & % HBM roofline; batched solves/s, p99 vs plain"
 UNIT = "MLUPS"
-BYTES_PER_LUP = 25          # read + write rho-1, jx, jy (FP32) + 1 B node type
+BYTES_PER_LUP = 24          # read + write rho-1, jx, jy (FP32)
+MASK_BYTES_PER_LUP = 1      # the node type, read by tiles with walls only
 FALLBACK_HBM_GBS = 6800.0   # used only when MEASURED_PEAKS.json is absent
-KERNEL_SRC = os.path.join(ROOT, "paper_1912_09327_gb300", "csrc", "lbm_step.cu")
+KERNEL_SRC = os.path.join(ROOT, "paper_1912_09327_gb300", "csrc",
+                          "lbm_kernels.cuh")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "lbm_step_kernel_f32.traffic.txt")
 
 
@@ -64,6 +66,12 @@ def parse_args(argv=None):
     ap.add_argument("--porous-cap", type=int, default=50000,
                     help="step cap of the porous run to residual 1e-8")
     ap.add_argument("--serving-requests", type=int, default=32)
+    ap.add_argument("--serving-cap", type=int, default=10000,
+                    help="step cap per served request")
+    ap.add_argument("--serving-full", action="store_true",
+                    help="configuration 5 as stated: 256 requests, each run "
+                         "to residual 1e-7 (cap 4e6 steps, far above what "
+                         "any request needs); takes tens of minutes")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args(argv)
 
@@ -205,8 +213,9 @@ def time_steps(dom, stream, steps):
 
 def bytes_per_lup(storage="f32"):
     """Algorithmic bytes per lattice update: rho - 1, jx, jy read and written
-    in the storage format, plus the 1-byte node type."""
-    return 1 + 6 * {"f32": 4, "f16": 2, "bf16": 2}[storage]
+    in the storage format (the paper's 2 N_f c per node, Eq. LBMTau1memory);
+    the node type (1 B, read only by tiles with walls) is not counted."""
+    return 6 * {"f32": 4, "f16": 2, "bf16": 2}[storage]
 
 
 def problem_domain(binding, p, stream, storage="f32"):
@@ -393,6 +402,38 @@ def run_e2e(binding, dom, n, steps, lanes=3):
                    "pinned host, one host thread per domain"}
 
 
+def run_multiphase(binding, stream, n=4096, steps=200):
+    """The multiphase drop of Section 4 (liquid disc in its periodic vapour,
+    Shan-Chen coupling g = -5), n x n, FP32: MLUPS of lbm_step(ctx, steps)
+    (one reduction at the end) beside the single-phase step on a periodic
+    box of the same size, after 200 steps that form the interface."""
+    import torch
+    from paper_1912_09327_gb300 import workloads as wl
+    out = {"workload": "drop in periodic vapour %dx%d, g = -5, FP32, %d timed "
+                       "steps (one reduction at the end)" % (n, n, steps)}
+    for name, p in (("multiphase", wl.drop(n)),
+                    ("single_phase", wl.periodic_box_tiled(n))):
+        d = binding.Domain.from_problem(p, stream=stream)
+        d.step(200)
+        stream.synchronize()
+        s = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        d.step(steps)
+        e.record(stream)
+        stream.synchronize()
+        ms = s.elapsed_time(e)
+        res, mass = d.residual()
+        out[name] = {"mlups": round(n * n * steps / (ms * 1e3), 1),
+                     "ms_per_step": round(ms / steps, 4),
+                     "variant": d.variant(), "residual": res}
+        d.close()
+        torch.cuda.empty_cache()
+    out["multiphase_over_single"] = round(out["multiphase"]["mlups"] /
+                                          out["single_phase"]["mlups"], 3)
+    return out
+
+
 def run_porous(binding, stream, n=4096, tol=1e-8, cap=50000, check=2000):
     """The porous-medium configuration: n x n periodic sample of seeded discs
     (radius 8..24, solid fraction 0.30), force 1e-5, run in FP32 to residual
@@ -509,26 +550,43 @@ def run_batched(binding, domains, steps, storage="f32"):
             "speedup": round(t_plain / t_batch, 2)}
 
 
-def run_serving(requests_n, cap=10000):
+def run_serving(requests_n, cap=10000, full=False):
     """Configuration: Poisson arrivals (seeded, 200 requests/s) of channel,
     cavity and porous solves with sides log-uniform in [64, 2048], each run to
     residual 1e-7 (capped at `cap` steps, reported), admitted by free device
-    memory; continuous batching against the plain sequential form."""
+    memory; continuous batching against the plain sequential form.  `full`:
+    the processor-sharing comparison is left out (its time is the same)."""
     from paper_1912_09327_gb300 import serving, workloads as wl
     reqs = wl.request_stream(requests_n, rate=200.0, seed=0)
+    kinds = {q.rid: q for q in reqs}
+
+    def log(form):
+        def on_done(r):   # progress on stderr: long runs leave a record
+            q = kinds[r.rid]
+            print("serving %s: request %d %s %dx%d done after %d steps, "
+                  "residual %.3g, latency %.3f s" % (form, r.rid, q.kind, q.nx,
+                                                    q.ny, r.steps, r.residual,
+                                                    r.latency),
+                  file=sys.stderr, flush=True)
+        return on_done if full else None
+
     srv = serving.Server(capacity=max(requests_n, 8), chunk=200,
                          residual_tol=1e-7, max_steps=cap)
-    batched = serving.summary(srv.run(reqs))
+    batched_results = srv.run(reqs, on_done=log("batched"))
+    batched = serving.summary(batched_results)
     srv.close()
-    # every request admitted at once, in arrival order (processor sharing)
-    srv = serving.Server(capacity=max(requests_n, 8), chunk=200,
-                         residual_tol=1e-7, max_steps=cap, policy="fifo",
-                         max_active_nodes=None)
-    shared = serving.summary(srv.run(reqs))
-    srv.close()
+    shared = None
+    if not full:
+        # every request admitted at once, in arrival order (processor sharing)
+        srv = serving.Server(capacity=max(requests_n, 8), chunk=200,
+                             residual_tol=1e-7, max_steps=cap, policy="fifo",
+                             max_active_nodes=None)
+        shared = serving.summary(srv.run(reqs))
+        srv.close()
     plain = serving.summary(serving.serve_sequential(reqs, chunk=200,
                                                      residual_tol=1e-7,
-                                                     max_steps=cap))
+                                                     max_steps=cap,
+                                                     on_done=log("plain")))
     return {"workload": "%d requests, Poisson 200/s, sides log-uniform "
                         "64..2048, residual 1e-7, cap %d steps, chunk 200"
                         % (requests_n, cap),
@@ -536,7 +594,13 @@ def run_serving(requests_n, cap=10000):
             "policy": "smallest first, %d Mi active nodes, 2 s wait bound"
                       % (serving.DEFAULT_ACTIVE_NODES >> 20),
             "continuous_batching_fifo_unbounded": shared,
-            "plain_sequential": plain}
+            "plain_sequential": plain,
+            "per_request": [{"rid": r.rid, "kind": q.kind, "nx": q.nx,
+                             "ny": q.ny, "steps": r.steps,
+                             "residual": r.residual,
+                             "latency_s": round(r.latency, 4)}
+                            for q, r in zip(reqs, batched_results)]
+            if full else None}
 
 
 def cpu_baseline(size, rows=1024, seconds=10.0):
@@ -719,6 +783,7 @@ def main(argv=None):
         line["sweep_bf16"] = run_sweep(binding, stream, sizes, "bf16")
         line["cavity_1024"] = run_cavity(binding, stream)
         line["porous_4096"] = run_porous(binding, stream, cap=args.porous_cap)
+        line["multiphase_4096"] = run_multiphase(binding, stream)
         line["precision"] = run_precision(binding, stream)
     if rank == 0 and not args.no_batched:
         line["batched"] = run_batched(binding, args.batched_domains,
@@ -726,7 +791,11 @@ def main(argv=None):
         line["batched_f16"] = run_batched(
             binding, args.batched_domains, args.batched_steps, storage="f16")
     if rank == 0 and not args.no_serving:
-        line["serving"] = run_serving(args.serving_requests)
+        if args.serving_full:
+            line["serving"] = run_serving(256, cap=4000000, full=True)
+        else:
+            line["serving"] = run_serving(args.serving_requests,
+                                          cap=args.serving_cap)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(n)
     if rank == 0:

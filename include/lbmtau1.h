@@ -96,7 +96,23 @@ typedef struct lbm_params {
   double fy;
   int32_t storage;    /* LBM_STORAGE_F32, _F16 or _BF16 */
   int32_t rounding;   /* LBM_ROUND_DEFAULT (0), _NEAREST or _STOCHASTIC */
+  double sc_g;        /* Shan-Chen coupling g of the multiphase step; 0 (the
+                         default) is the single-phase step.  See below. */
 } lbm_params;
+
+/*
+ * Multiphase step (Section 4): with sc_g != 0 every pulled neighbour's
+ * momentum also gets the pseudo-potential force of Eq. (f_sc),
+ *   F_SC(x) = -g psi(x) sum_i w_i psi(x + e_i) e_i,  psi = 1 - exp(-rho),
+ * (Shan and Chen's model: alpha_i = w_i, G(e_i) = -g e_i; psi = 0 at solid
+ * nodes and outside non-periodic edges; g < -4 separates a liquid and its
+ * vapour), added beside the body force before the division by the density,
+ * where Algorithm 1 adds the body force.  At tau = 1 this velocity shift is
+ * also Kupershtokh's exact-difference forcing.  The potential of every node
+ * is computed once per step from the density the kernel streams, so no
+ * potential field is stored.  FP32 storage only; batches take single-phase
+ * members only.
+ */
 
 typedef struct lbm_ctx lbm_ctx;
 
@@ -235,6 +251,30 @@ int lbm_set_step_count(lbm_ctx *ctx, int64_t steps);
 int lbm_residual(lbm_ctx *ctx, double *residual, double *mass);
 
 /*
+ * A termination test that rounding noise cannot hold off.  The residual
+ * above compares consecutive steps, so it cannot fall below the noise of
+ * the stored values: about one unit in the last place per step, 6e-4 for
+ * FP16 and 5e-3 for BF16 stochastic storage, and near 6e-8 for some FP32
+ * flows.  Section 3 tests convergence by the change between states
+ * Delta t = 1000 steps apart (the cavity's flux check); these calls measure
+ * the velocity change over any span:
+ *   lbm_snapshot copies the current state into caller-owned device memory
+ *   (256-byte aligned, lbm_snapshot_bytes(p) bytes, asynchronous);
+ *   lbm_change_since returns, `steps` steps later,
+ *     change = sqrt(sum |u_now - u_snap|^2 / sum |u_now|^2) / steps
+ *   over fluid nodes (u = j / rho, FP64 sums; the plain sqrt of the first
+ *   sum over steps when the flow is at rest): the mean relative velocity
+ *   change per step over the span.  Noise of n units in the last place then
+ *   adds only about n ulp / steps.  Synchronises the stream.
+ * Errors: LBM_E_INVAL (null, misaligned or small buffer, steps < 1),
+ * LBM_E_STATE, LBM_E_CUDA.
+ */
+size_t lbm_snapshot_bytes(const lbm_params *p);
+int lbm_snapshot(lbm_ctx *ctx, void *dev_buf, size_t bytes);
+int lbm_change_since(lbm_ctx *ctx, const void *dev_buf, int64_t steps,
+                     double *change);
+
+/*
  * One step that allocates no memory (the paper has no counterpart; this is
  * an interface for callers that cannot allocate device memory themselves,
  * such as an application that hands all device memory to its own pool
@@ -311,8 +351,9 @@ int lbm_batch_create(int32_t capacity, int64_t max_tiles, void *dev_workspace,
                      lbm_batch **out);
 
 /* Adds a context (same stream and storage format as the other members,
- * geometry set) and returns its slot; the context must outlive its
- * membership.  Errors: LBM_E_INVAL, LBM_E_STATE, LBM_E_WORKSPACE (full). */
+ * geometry set, single phase) and returns its slot; the context must outlive
+ * its membership.  Errors: LBM_E_INVAL (also a multiphase context),
+ * LBM_E_STATE, LBM_E_WORKSPACE (full). */
 int lbm_batch_add(lbm_batch *b, lbm_ctx *ctx, int32_t *slot);
 
 /* Removes the member in `slot` (between steps).  Errors: LBM_E_INVAL. */

@@ -49,7 +49,8 @@ class lbm_params(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int64), ("ny", ctypes.c_int64),
                 ("periodic_x", ctypes.c_int32), ("periodic_y", ctypes.c_int32),
                 ("fx", ctypes.c_double), ("fy", ctypes.c_double),
-                ("storage", ctypes.c_int32), ("rounding", ctypes.c_int32)]
+                ("storage", ctypes.c_int32), ("rounding", ctypes.c_int32),
+                ("sc_g", ctypes.c_double)]
 
 
 _P = ctypes.POINTER(lbm_params)
@@ -75,6 +76,13 @@ _lib.lbm_variant.argtypes = [_vp]
 _lib.lbm_variant.restype = ctypes.c_int32
 _lib.lbm_set_copy_wait_ns.argtypes = [_vp, ctypes.c_int64]
 _lib.lbm_set_copy_wait_ns.restype = ctypes.c_int
+_lib.lbm_snapshot_bytes.argtypes = [_P]
+_lib.lbm_snapshot_bytes.restype = ctypes.c_size_t
+_lib.lbm_snapshot.argtypes = [_vp, _vp, ctypes.c_size_t]
+_lib.lbm_snapshot.restype = ctypes.c_int
+_lib.lbm_change_since.argtypes = [_vp, _vp, ctypes.c_int64,
+                                  ctypes.POINTER(ctypes.c_double)]
+_lib.lbm_change_since.restype = ctypes.c_int
 _lib.lbm_moments.argtypes = [_vp, _vp, _vp, _vp]
 _lib.lbm_moments.restype = ctypes.c_int
 _lib.lbm_get_state.argtypes = [_vp, _vp, _vp, _vp]
@@ -149,12 +157,12 @@ def _check(status, ctx=None):
 
 def make_params(nx, ny, periodic=(False, False), force=(0.0, 0.0),
                 storage=LBM_STORAGE_F32,
-                rounding=LBM_ROUND_DEFAULT) -> lbm_params:
+                rounding=LBM_ROUND_DEFAULT, sc_g=0.0) -> lbm_params:
     if isinstance(rounding, str):
         rounding = ROUNDING_NAMES[rounding]
     return lbm_params(int(nx), int(ny), int(bool(periodic[0])),
                       int(bool(periodic[1])), float(force[0]), float(force[1]),
-                      int(storage), int(rounding))
+                      int(storage), int(rounding), float(sc_g))
 
 
 def _ptr(a):
@@ -420,14 +428,14 @@ class Domain:
 
     def __init__(self, nx, ny, periodic=(False, False), force=(0.0, 0.0),
                  device="cuda", stream=None, storage=LBM_STORAGE_F32,
-                 rounding=LBM_ROUND_DEFAULT):
+                 rounding=LBM_ROUND_DEFAULT, sc_g=0.0):
         import torch
         self.nx, self.ny = int(nx), int(ny)
         if isinstance(storage, str):
             storage = STORAGE_NAMES[storage]
         self.storage = int(storage)
         self.params = make_params(nx, ny, periodic, force, self.storage,
-                                  rounding)
+                                  rounding, sc_g)
         nbytes = lbm_workspace_bytes(self.params)
         if nbytes == 0:
             raise LbmError(LBM_E_INVAL, "invalid domain parameters")
@@ -440,6 +448,8 @@ class Domain:
     @classmethod
     def from_problem(cls, prob, **kw):
         ny, nx = prob.mask.shape
+        if "sc_g" in prob.meta and "sc_g" not in kw:
+            kw["sc_g"] = prob.meta["sc_g"]
         d = cls(nx, ny, prob.periodic, prob.force, **kw)
         d.set_geometry(prob.mask)
         d.set_moments(prob.rho, prob.jx, prob.jy)
@@ -459,6 +469,23 @@ class Domain:
 
     def set_copy_wait_ns(self, ns):
         lbm_set_copy_wait_ns(self.ctx, ns)
+
+    def snapshot(self):
+        """A device copy of the current state (a torch buffer) to measure
+        the change over a span of steps against (change_since)."""
+        import torch
+        n = _lib.lbm_snapshot_bytes(ctypes.byref(self.params))
+        buf = torch.empty(n, dtype=torch.uint8, device=self.device)
+        _check(_lib.lbm_snapshot(self.ctx, _vp(buf.data_ptr()), n), self.ctx)
+        return buf
+
+    def change_since(self, snap, steps):
+        """Mean relative velocity change per step since `snap` was taken,
+        `steps` steps ago."""
+        out = ctypes.c_double()
+        _check(_lib.lbm_change_since(self.ctx, _vp(snap.data_ptr()),
+                                     int(steps), ctypes.byref(out)), self.ctx)
+        return out.value
 
     def step_count(self):
         return lbm_step_count(self.ctx)

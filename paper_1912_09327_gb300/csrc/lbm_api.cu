@@ -34,7 +34,8 @@ bool params_ok(const lbm_params *p) {
          (p->rounding == LBM_ROUND_DEFAULT ||
           p->rounding == LBM_ROUND_NEAREST ||
           p->rounding == LBM_ROUND_STOCHASTIC) &&
-         isfinite(p->fx) && isfinite(p->fy);
+         isfinite(p->fx) && isfinite(p->fy) && isfinite(p->sc_g) &&
+         (p->sc_g == 0.0 || p->storage == LBM_STORAGE_F32);
 }
 
 Layout make_layout(const lbm_params *p) {
@@ -405,6 +406,7 @@ int lbm_step(lbm_ctx *c, int64_t nsteps) {
   a.periodic_y = c->p.periodic_y != 0;
   a.fx = static_cast<float>(c->p.fx);
   a.fy = static_cast<float>(c->p.fy);
+  a.g_sc = static_cast<float>(c->p.sc_g);
   a.partials = c->partials;
   a.flag = c->flag;
   a.storage = c->p.storage;
@@ -521,6 +523,67 @@ int lbm_moments(lbm_ctx *c, double *rho, double *jx, double *jy) {
   }
   cudaError_t e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamSynchronize");
+  c->err[0] = '\0';
+  return LBM_OK;
+}
+
+size_t lbm_snapshot_bytes(const lbm_params *p) {
+  if (!params_ok(p)) return 0;
+  return 3 * make_layout(p).field_bytes;
+}
+
+int lbm_snapshot(lbm_ctx *c, void *dev_buf, size_t bytes) {
+  if (!c) return LBM_E_INVAL;
+  if (!dev_buf || reinterpret_cast<uintptr_t>(dev_buf) % kAlign ||
+      bytes < 3 * c->L.field_bytes)
+    return fail(c, LBM_E_INVAL, "snapshot buffer missing, misaligned or small");
+  if (!c->has_geometry)
+    return fail(c, LBM_E_STATE, "lbm_set_geometry has not been called");
+  int st = bind_device(c);
+  if (st) return st;
+  // the three planes of the current copy are contiguous in the workspace
+  cudaError_t e = cudaMemcpyAsync(dev_buf, c->f[c->cur].d,
+                                  3 * c->L.field_bytes,
+                                  cudaMemcpyDeviceToDevice, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpyAsync(snapshot)");
+  c->err[0] = '\0';
+  return LBM_OK;
+}
+
+int lbm_change_since(lbm_ctx *c, const void *dev_buf, int64_t steps,
+                     double *change) {
+  if (!c) return LBM_E_INVAL;
+  if (!dev_buf || reinterpret_cast<uintptr_t>(dev_buf) % kAlign || steps < 1 ||
+      !change)
+    return fail(c, LBM_E_INVAL, "bad snapshot buffer, step count or output");
+  if (!c->has_geometry)
+    return fail(c, LBM_E_STATE, "lbm_set_geometry has not been called");
+  int st = bind_device(c);
+  if (st) return st;
+  const char *b = static_cast<const char *>(dev_buf);
+  lbmtau1::Fields snap;
+  snap.d = const_cast<char *>(b);
+  snap.jx = const_cast<char *>(b + c->L.field_bytes);
+  snap.jy = const_cast<char *>(b + 2 * c->L.field_bytes);
+  // the reduction partials of the step serve as scratch (the step's own
+  // result slot is not touched); one block of four warps per partial block
+  int64_t blocks = (c->p.nx * c->p.ny + 127) / 128;
+  if (blocks > c->L.nblocks) blocks = c->L.nblocks;
+  if (blocks > 4096) blocks = 4096;
+  double *out = c->result + 4;
+  cudaError_t e = lbmtau1::launch_change(c->p.storage, c->f[c->cur], snap,
+                                         c->mask, c->p.nx, c->p.ny,
+                                         c->L.pitch, c->partials, blocks,
+                                         c->stream);
+  if (e == cudaSuccess)
+    e = lbmtau1::launch_finalize(c->partials, blocks, out, c->stream);
+  double h[3];
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h, out, sizeof h, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "change reduction");
+  const double rel = h[1] > 0.0 ? sqrt(h[0] / h[1]) : sqrt(h[0]);
+  *change = rel / static_cast<double>(steps);
   c->err[0] = '\0';
   return LBM_OK;
 }

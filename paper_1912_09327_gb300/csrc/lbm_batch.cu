@@ -334,6 +334,8 @@ int lbm_batch_add(lbm_batch *b, lbm_ctx *ctx, int32_t *slot) {
     return bfail(b, LBM_E_INVAL, "member must use the batch's stream");
   if (!ctx->has_geometry)
     return bfail(b, LBM_E_STATE, "member has no geometry");
+  if (ctx->p.sc_g != 0.0)
+    return bfail(b, LBM_E_INVAL, "multiphase domains are stepped alone");
   if (lbm_batch_members(b) > 0 && ctx->p.storage != b->storage)
     return bfail(b, LBM_E_INVAL, "members must share one storage format");
   for (lbm_ctx *c : b->slots)

@@ -73,9 +73,20 @@ constexpr unsigned kFull = 0xffffffffu;
 
 // D2Q9 weights (rest 4/9, axis 1/9, diagonal 1/36) and the combinations of
 // them that appear in the closed form.
+// The density a node receives is the weighted sum of its nine sources'
+// densities, so the three weights must sum to exactly one in FP32 as well,
+// or every step scales the density deviations by their sum (by 1 + 7.5e-9
+// with the nearest FP32 values, which drains a multiphase drop of order-one
+// deviations by 1e-5 of its mass in 2000 steps).  4/9 and 1/9 are the
+// nearest FP32 values; the diagonal weight is one unit in the last place
+// below the nearest value of 1/36 (6.7e-8 relative), which makes
+// k4_9 + 4 k1_9 + 4 k1_36 == 1 exactly.
 constexpr float k4_9 = 4.0f / 9.0f;
 constexpr float k1_9 = 1.0f / 9.0f;
-constexpr float k1_36 = 1.0f / 36.0f;
+constexpr float k1_36 = 0x1.c71c70p-6f;
+static_assert(static_cast<double>(k4_9) + 4.0 * static_cast<double>(k1_9) +
+                      4.0 * static_cast<double>(k1_36) == 1.0,
+              "D2Q9 weights must sum to one in FP32");
 constexpr float k1_12 = 1.0f / 12.0f;  // 3 * (1/36)
 constexpr float k1_3 = 1.0f / 3.0f;    // 3 * (1/9)
 constexpr float k1_6 = 1.0f / 6.0f;    // 2 * (1/12)
@@ -177,8 +188,11 @@ __device__ __forceinline__ void store_pairs(T *p, const float2 (&v)[kC / 2],
   } u;
 #pragma unroll
   for (int q = 0; q < kC / 2; ++q) {
-    u.e[2 * q] = Storage<T>::encode(v[q].x * scale);
-    u.e[2 * q + 1] = Storage<T>::encode(v[q].y * scale);
+    const float2 f = std::is_same<T, float>::value
+                         ? v[q]
+                         : __fmul2_rn(v[q], make_float2(scale, scale));
+    u.e[2 * q] = Storage<T>::encode(f.x);
+    u.e[2 * q + 1] = Storage<T>::encode(f.y);
   }
   *reinterpret_cast<V *>(p) = u.v;
 }
@@ -212,23 +226,38 @@ __device__ __forceinline__ uint32_t pack_sr(__nv_bfloat16, float lo, float hi,
   return d;
 }
 
-// store_pairs of a 16-bit format with stochastic rounding; `key` identifies
-// (row, step, field) and `x` is the first column (each pair of columns draws
-// one hashed word).
+// One output row (three fields) of a 16-bit format with stochastic
+// rounding, kC / 2 column pairs each: one hashed word per column pair, from
+// `key` (row and step) and the pair's first column x + 2q; the fields take
+// that word rotated by 0, 11 and 22 bits.
 template <int kC, typename T>
-__device__ __forceinline__ void store_pairs_sr(T *p, const float2 (&v)[kC / 2],
-                                               float scale, uint32_t key,
-                                               uint32_t x) {
+__device__ __forceinline__ void store_row_sr(T *dd, T *dx, T *dy,
+                                             const float2 (&d)[kC / 2],
+                                             const float2 (&jx)[kC / 2],
+                                             const float2 (&jy)[kC / 2],
+                                             uint32_t key, uint32_t x) {
   static_assert(kC % 2 == 0, "pairs of columns");
-  uint32_t w[kC / 2];
+  const float2 sd = make_float2(Storage<T>::kD, Storage<T>::kD);
+  const float2 sj = make_float2(Storage<T>::kJ, Storage<T>::kJ);
+  uint32_t wd[kC / 2], wx[kC / 2], wy[kC / 2];
 #pragma unroll
-  for (int q = 0; q < kC / 2; ++q)
-    w[q] = pack_sr(T(), v[q].x * scale, v[q].y * scale,
-                   fmix32(key + (x + 2u * q) * 0x9e3779b1u));
-  if constexpr (kC == 4)
-    *reinterpret_cast<uint2 *>(p) = make_uint2(w[0], w[1]);
-  else
-    *reinterpret_cast<uint32_t *>(p) = w[0];
+  for (int q = 0; q < kC / 2; ++q) {
+    const uint32_t h = fmix32(key + (x + 2u * q) * 0x9e3779b1u);
+    const float2 a = __fmul2_rn(d[q], sd), b = __fmul2_rn(jx[q], sj),
+                 c = __fmul2_rn(jy[q], sj);
+    wd[q] = pack_sr(T(), a.x, a.y, h);
+    wx[q] = pack_sr(T(), b.x, b.y, __funnelshift_l(h, h, 11));
+    wy[q] = pack_sr(T(), c.x, c.y, __funnelshift_l(h, h, 22));
+  }
+  if constexpr (kC == 4) {
+    *reinterpret_cast<uint2 *>(dd) = make_uint2(wd[0], wd[1]);
+    *reinterpret_cast<uint2 *>(dx) = make_uint2(wx[0], wx[1]);
+    *reinterpret_cast<uint2 *>(dy) = make_uint2(wy[0], wy[1]);
+  } else {
+    *reinterpret_cast<uint32_t *>(dd) = wd[0];
+    *reinterpret_cast<uint32_t *>(dx) = wx[0];
+    *reinterpret_cast<uint32_t *>(dy) = wy[0];
+  }
 }
 
 // FP32 storage with stochastic rounding: the dither, uniform in (-1/2, 1/2)
@@ -358,9 +387,11 @@ __device__ __forceinline__ void fence_async_shared() {
 // Geometry of one ring stage for kC columns per lane: the field window starts
 // at ws, the 16-byte boundary at or below the warp's first column x0 - kC,
 // and covers its kLanes * kC columns; the node-type window starts at the
-// 16-byte boundary at or below ws.  A side slot after them holds, on a
-// periodic x axis, the 16-byte blocks (three fields, node types) that start
-// the row: column nx seen from the domain's last column.
+// 16-byte boundary at or below ws.  Two side slots after them hold, on a
+// periodic x axis, 16-byte blocks (three fields, node types) from the other
+// end of the row: the first the blocks that start the row (columns nx and
+// nx + 1 seen from the domain's last column), the second (multiphase step)
+// the blocks holding column nx - 2 (column -2 seen from the first).
 template <int kC, typename T>
 struct Stage {
   static constexpr int kAlignElems = 16 / static_cast<int>(sizeof(T));
@@ -368,7 +399,7 @@ struct Stage {
       (kAlignElems - 1 + kLanes * kC + kAlignElems - 1) / kAlignElems * kAlignElems;
   static constexpr int kFieldBytes = kWin * static_cast<int>(sizeof(T));
   static constexpr int kMaskBytes = (kWin + 15 + 15) / 16 * 16;
-  static constexpr int kSideBytes = 4 * 16;
+  static constexpr int kSideBytes = 8 * 16;
   static constexpr int kBytes = 3 * kFieldBytes + kMaskBytes + kSideBytes;
 };
 
@@ -425,8 +456,10 @@ __host__ __device__ constexpr int smem_bytes() {
 // the warp calls it; no other warp takes part.  kClean: the warp tile's
 // marched rows and columns all lie inside the domain and hold fluid nodes
 // only (see tile_flags_kernel), so node types, edges and wall terms need no
-// handling and the node-type rows are not copied.
-template <typename T, int kC, int kRows, int kS, bool kReduce, bool kClean>
+// handling and the node-type rows are not copied.  kSC: the Shan-Chen
+// multiphase step (Section 4, Eq. f_sc), see the force pipeline below.
+template <typename T, int kC, int kRows, int kS, bool kReduce, bool kClean,
+          bool kSC = false>
 __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
                                           int64_t by, int w, int slot,
                                           int64_t gx, const SolidSums *lut,
@@ -488,7 +521,11 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
   // FP32 storage with stochastic rounding: this step's dither
   const float2 dither = bc(kF32 && a.sr ? fp32_dither(a.step) : 0.0f);
 
-  float2 rs_num = bc(0.f), rs_den = bc(0.f), rs_mass = bc(0.f);
+  // Residual sums in FP32 per lane; the mass in FP64, each row's FP32 sum of
+  // a lane's (at most four) nodes added to it: densities of order one (the
+  // multiphase step) keep their precision over a tile's rows.
+  float2 rs_num = bc(0.f), rs_den = bc(0.f);
+  double rs_mass = 0.0;
   float rmin = 1.0f;
 
   if (y0 < a.ny) {
@@ -496,16 +533,22 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
     const int ty0 = static_cast<int>(y0), ty1 = static_cast<int>(y1);
     const int tny = static_cast<int>(a.ny);
     const int npairs = (ty1 - ty0 + 1) / 2 + 1;
-    const int nrows = 2 * npairs;  // source rows y0 - 1 .. y0 - 2 + nrows
-    // source row of ring index i: -1 for a solid row beyond a wall-less edge
+    // Ring rows: the source rows y0 - 1 .. y0 - 2 + 2 npairs and, for the
+    // multiphase step, one more row above and below them whose potential the
+    // force of the outermost source rows needs (kLead: rows before the
+    // first source row).
+    constexpr int kLead = kSC ? 1 : 0;
+    const int nrows = 2 * npairs + 2 * kLead;
+    // grid row of ring index i: -1 for a solid row beyond a wall-less edge
     auto source_row = [&](int i) -> int {
-      const int r = ty0 - 1 + i;
+      const int r = ty0 - 1 - kLead + i;
       if (r >= 0 && r < tny) return r;
       return a.periodic_y ? static_cast<int>(wrap_index(r, tny)) : -1;
     };
-    auto issue = [&](int i) {  // lane 0 only
-      const int r = source_row(i);
-      const int st = static_cast<int>(static_cast<unsigned>(i) % kS);
+    // starts the copies of ring row i into stage st (lane 0 only)
+    auto issue = [&](int i, int st) {
+      // a clean tile's rows all lie inside the domain
+      const int r = kClean ? ty0 - 1 - kLead + i : source_row(i);
       uint64_t *bar = bars + st;
       if (r < 0) {  // solid row: nothing to copy, but the phase still completes
         mbar_arrive(bar);
@@ -534,7 +577,8 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
       const uint32_t fbytes = static_cast<uint32_t>((c1 - c0) * sizeof(T));
       const uint32_t mbytes = kClean ? 0u : static_cast<uint32_t>(k1 - k0);
       mbar_expect_tx(bar, 3 * fbytes + mbytes + (wrap_l ? 64u : 0u) +
-                              (wrap_r ? 64u : 0u));
+                              (wrap_r ? 64u : 0u) +
+                              (kSC && wrap_l ? 64u : 0u));
       const int64_t rp = static_cast<int64_t>(r) * a.pitch;
       const T *src[3] = {static_cast<const T *>(a.src.d) + rp,
                          static_cast<const T *>(a.src.jx) + rp,
@@ -558,6 +602,14 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
         for (int f = 0; f < 3; ++f) bulk_copy(side + 16 * f, src[f], 16u, bar);
         bulk_copy(side + 48, mrow, 16u, bar);
       }
+      if (kSC && wrap_l) {  // the blocks holding column -2, second side slot
+        unsigned char *side2 = dmask + St::kMaskBytes + 64;
+        const int64_t l2 = a.nx >= 2 ? a.nx - 2 : 0;
+#pragma unroll
+        for (int f = 0; f < 3; ++f)
+          bulk_copy(side2 + 16 * f, src[f] + (l2 & ~(kA - 1)), 16u, bar);
+        bulk_copy(side2 + 48, mrow + (l2 & ~int64_t(15)), 16u, bar);
+      }
     };
     // value v into column `col` (0 .. kC - 1) of a row of pairs
     auto set_col = [](float2 (&p)[kP], int col, float v) {
@@ -567,12 +619,11 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
         if (col == 2 * q + 1) p[q].y = v;
       }
     };
-    // ring row i -> registers; false when the copy did not arrive in time
-    auto fetch = [&](int i, Row &o) -> bool {
+    // ring row i, in stage st with phase parity ph -> registers; false when
+    // the copy did not arrive in time
+    auto fetch = [&](int i, int st, unsigned ph, Row &o) -> bool {
       if constexpr (kClean) {  // an in-domain row of fluid nodes
-        const unsigned ui = static_cast<unsigned>(i);
-        const int st = static_cast<int>(ui % kS);
-        const bool ok = mbar_wait(bars + st, (ui / kS) & 1u, a.wait_ns);
+        const bool ok = mbar_wait(bars + st, ph, a.wait_ns);
         const unsigned char *src = stages + st * St::kBytes;
         load_pairs<kC, T>(reinterpret_cast<const T *>(src) + c_lane, o.d,
                           1.0f / SS::kD);
@@ -593,9 +644,7 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
         o.fluid = 0u;
         return true;
       }
-      const unsigned ui = static_cast<unsigned>(i);
-      const int st = static_cast<int>(ui % kS);
-      const bool ok = mbar_wait(bars + st, (ui / kS) & 1u, a.wait_ns);
+      const bool ok = mbar_wait(bars + st, ph, a.wait_ns);
       const unsigned char *src = stages + st * St::kBytes;
       const T *fd = reinterpret_cast<const T *>(src);
       const T *fx_ = reinterpret_cast<const T *>(src + St::kFieldBytes);
@@ -632,6 +681,33 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
         o.solid = (o.solid & ~bit) | ((t == 1u) ? bit : 0u);
         o.fluid = (o.fluid & ~bit) | ((t == 0u) ? bit : 0u);
       }
+      if constexpr (kSC) {
+        // The multiphase force of columns -1 and nx needs the potential of
+        // columns -2 and nx + 1 on a periodic x axis: their density and node
+        // type (nothing else of theirs reaches an output) from the second
+        // side slot and the first.
+        auto patch = [&](int col, float d, unsigned t) {
+          set_col(o.d, col, d);
+          const unsigned bit = 1u << col;
+          o.solid = (o.solid & ~bit) | ((t == 1u) ? bit : 0u);
+          o.fluid = (o.fluid & ~bit) | ((t == 0u) ? bit : 0u);
+        };
+        const unsigned char *side = mw + St::kMaskBytes;
+        if (wrap_l && xb < 0) {  // column -2: column nx - 2 (0 for nx < 2)
+          const int64_t l2 = a.nx >= 2 ? a.nx - 2 : 0;
+          const T *f2 = reinterpret_cast<const T *>(side + 64);
+          patch(kC - 2,
+                SS::decode(f2[l2 & (St::kAlignElems - 1)]) * (1.0f / SS::kD),
+                side[64 + 48 + (l2 & 15)]);
+        }
+        if (wrap_r && xb <= a.nx + 1 && a.nx + 1 < xb + kC) {
+          // column nx + 1: column 1 (0 for nx < 2), in the first side slot
+          const int r2 = a.nx >= 2 ? 1 : 0;
+          const T *f1 = reinterpret_cast<const T *>(side);
+          patch(static_cast<int>(a.nx + 1 - xb),
+                SS::decode(f1[r2]) * (1.0f / SS::kD), side[48 + r2]);
+        }
+      }
       return ok;
     };
 
@@ -648,9 +724,70 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
     rb.solid = rb.fluid = 0u;
     unsigned pS6 = 0u, ppS6 = 0u;  // solid bits (cols -1..kC) of rows s-1, s-2
 
+    // The multiphase force (kSC), F_SC(x) = -g psi(x) sum_i w_i psi(x + e_i)
+    // e_i (Eq. f_sc with Shan and Chen's psi = 1 - exp(-rho), alpha_i = w_i,
+    // G(e_i) = -g e_i; psi = 0 at solid nodes and outside non-periodic
+    // edges), needs the potentials of the rows above and below a source row.
+    // The ring holds one row more above and below the source rows; when
+    // source row s is taken, row s + 1 is read from its stage as well (it
+    // stays there until taken in turn) and its potential terms computed
+    // once.  With A = right - left and S = right + left of a row's
+    // potentials and C the potentials themselves,
+    //   F_SC(s) = -g C(s) (A(s)/9 + (A(s-1) + A(s+1))/36,
+    //                      (C(s+1) - C(s-1))/9 + (S(s+1) - S(s-1))/36):
+    // the rows above and below are combined first, so the force is exactly
+    // odd under either mirror of the lattice, in floating point too, and a
+    // symmetric drop feels no net force.  The terms of rows s - 1 and s are
+    // carried, in two sets that swap roles each row as the row buffers do.
+    const float2 mg = bc(-a.g_sc);
+    // potential of a row's columns (C) and its horizontal differences and
+    // sums (A = right - left, S = right + left)
+    auto psi_terms = [&](const Row &r, float2 (&C)[kP], float2 (&A)[kP],
+                         float2 (&S)[kP]) {
+#pragma unroll
+      for (int q = 0; q < kP; ++q) {
+        const float2 rho = add(r.d[q], one);
+        const float2 e = make_float2(__expf(-rho.x), __expf(-rho.y));
+        const bool s0 = (r.solid >> (2 * q)) & 1u;
+        const bool s1 = (r.solid >> (2 * q + 1)) & 1u;
+        C[q] = make_float2(s0 ? 0.f : 1.0f - e.x, s1 ? 0.f : 1.0f - e.y);
+      }
+      const float hm = __shfl_up_sync(kFull, C[kP - 1].y, 1);
+      const float hp = __shfl_down_sync(kFull, C[0].x, 1);
+#pragma unroll
+      for (int q = 0; q < kP; ++q) {
+        const float2 L = make_float2(q == 0 ? hm : C[q - 1].y, C[q].x);
+        const float2 R =
+            make_float2(C[q].y, q == kP - 1 ? hp : C[q + 1].x);
+        A[q] = sub(R, L);
+        S[q] = add(R, L);
+      }
+    };
     // Source row s = ty0 - 1 + i, fetched into `cur`; `prev` holds row s - 1.
-    auto row = [&](int i, Row &cur, const Row &prev) {
+    // kSC: `nxt` holds row s + 1 (its density and node types are used),
+    // (pC, pA, pS) the potential terms of row s - 1, (cC, cA, cS) those of
+    // row s; row s + 1's replace row s - 1's.
+    auto row = [&](int i, Row &cur, const Row &prev, const Row &nxt,
+                   float2 (&pC)[kP], float2 (&pA)[kP], float2 (&pS)[kP],
+                   float2 (&cC)[kP], float2 (&cA)[kP], float2 (&cS)[kP]) {
       const int s = ty0 - 1 + i;
+      float2 Fsx[kP], Fsy[kP];  // F_SC of row s
+      if constexpr (kSC) {
+        float2 C1[kP], A1[kP], S1[kP];
+        psi_terms(nxt, C1, A1, S1);
+#pragma unroll
+        for (int q = 0; q < kP; ++q) {
+          const float2 k = mul(cC[q], mg);
+          const float2 sx = fma2(w1_36, add(pA[q], A1[q]), mul(w1_9, cA[q]));
+          const float2 sy =
+              fma2(w1_9, sub(C1[q], pC[q]), mul(w1_36, sub(S1[q], pS[q])));
+          Fsx[q] = mul(k, sx);
+          Fsy[q] = mul(k, sy);
+          pC[q] = C1[q];
+          pA[q] = A1[q];
+          pS[q] = S1[q];
+        }
+      }
       const int o = s - 1;                       // output row completed here
       const bool out_row = o >= ty0 && o < ty1;  // the same for the warp
       // Per-node quantities of row s, pre-scaled by the lattice weights they
@@ -661,15 +798,19 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
 #pragma unroll
       for (int q = 0; q < kP; ++q) {
         float2 dfj;
+        // z: the momentum a node brings as a source, its own j plus (kSC)
+        // its multiphase force; a solid node brings -F (zero momentum j + F)
+        const float2 jx = kSC ? add(cur.jx[q], Fsx[q]) : cur.jx[q];
+        const float2 jy = kSC ? add(cur.jy[q], Fsy[q]) : cur.jy[q];
         if constexpr (kClean) {
-          cur.zx[q] = cur.jx[q];
-          cur.zy[q] = cur.jy[q];
+          cur.zx[q] = jx;
+          cur.zy[q] = jy;
           dfj = cur.d[q];
         } else {
           const bool s0 = (cur.solid >> (2 * q)) & 1u;
           const bool s1 = (cur.solid >> (2 * q + 1)) & 1u;
-          cur.zx[q] = make_float2(s0 ? -fx : cur.jx[q].x, s1 ? -fx : cur.jx[q].y);
-          cur.zy[q] = make_float2(s0 ? -fy : cur.jy[q].x, s1 ? -fy : cur.jy[q].y);
+          cur.zx[q] = make_float2(s0 ? -fx : jx.x, s1 ? -fx : jx.y);
+          cur.zy[q] = make_float2(s0 ? -fy : jy.x, s1 ? -fy : jy.y);
           dfj = make_float2(s0 ? 0.f : cur.d[q].x, s1 ? 0.f : cur.d[q].y);
         }
         const float2 mx = add(cur.zx[q], F2x);  // j + F, 0 on solid nodes
@@ -715,6 +856,7 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
       }
 
       float2 od[kP], ox[kP], oy[kP];
+      float2 mrow = bc(0.f);  // this row's mass terms (kReduce)
 #pragma unroll
       for (int q = 0; q < kP; ++q) {
         const float2 KL = Ks[q], KR = Ks[q + 1];
@@ -743,14 +885,16 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
         const float2 Sdd = fma2(w4_9, R0[q], fma2(w1_3, mxd, add(KL, KR)));
         const float2 Smx = fma2(w1_3, hx, sub(KL, KR));
 
-        // Output row s - 1: the momentum in increment form, every j_P - j_O
-        // an exact difference; solid neighbours add their wall terms in
-        // place (nothing to add, and no zero terms, without solids).
+        // Output row s - 1: the momentum in increment form on the base z_O
+        // (j_O, plus F_SC(O) for the multiphase step), every z_P - z_O an
+        // exact difference; solid neighbours add their wall terms in place
+        // (nothing to add, and no zero terms, without solids).
         const float2 dO = prev.d[q], jxO = prev.jx[q], jyO = prev.jy[q];
+        const float2 zxO = prev.zx[q], zyO = prev.zy[q];
         float2 dn = add(acc_dd[q], sub(U, V));
-        float2 incx = fma2(w1_6, sub(zxC, jxO),
+        float2 incx = fma2(w1_6, sub(zxC, zxO),
                            add(add(acc_mx[q], sub(Up, Vp)), F2x));
-        float2 incy = fma2(half, sub(zyC, jyO),
+        float2 incy = fma2(half, sub(zyC, zyO),
                            add(add(acc_my[q], sub(Y, U)), F2y));
         if (!kClean && any_solid) {
 #pragma unroll
@@ -772,12 +916,12 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
         }
         if constexpr (kF32) {
           if (a.sr) {  // stochastic rounding of the stored momentum
-            incx = fma2(lead_pow2(jxO), dither, incx);
-            incy = fma2(lead_pow2(jyO), dither, incy);
+            incx = fma2(lead_pow2(zxO), dither, incx);
+            incy = fma2(lead_pow2(zyO), dither, incy);
           }
         }
-        const float2 mxn = add(jxO, incx);
-        const float2 myn = add(jyO, incy);
+        const float2 mxn = add(zxO, incx);
+        const float2 myn = add(zyO, incy);
         bool f0 = true, f1 = true;
         if constexpr (!kClean) {
           f0 = (prev.fluid >> (2 * q)) & 1u;
@@ -810,7 +954,7 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
             if (owner && out_row) {
               rs_num = add(rs_num, nn);
               rs_den = add(rs_den, dd2);
-              rs_mass = add(rs_mass, dn);
+              mrow = add(mrow, dn);
               rmin = fminf(rmin, fminf(rn.x, rn.y));
             }
           } else {
@@ -819,13 +963,13 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
             if (v0) {
               rs_num.x += nn.x;
               rs_den.x += dd2.x;
-              rs_mass.x += dn.x;
+              mrow.x += dn.x;
               rmin = fminf(rmin, rn.x);
             }
             if (v1) {
               rs_num.y += nn.y;
               rs_den.y += dd2.y;
-              rs_mass.y += dn.y;
+              mrow.y += dn.y;
               rmin = fminf(rmin, rn.y);
             }
           }
@@ -833,12 +977,14 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
         // carry to output row s: South(s - 1) + Same(s) and the vertical
         // difference with row s - 1 (j of row s is the base of its nodes)
         acc_dd[q] = add(t_dd[q], Sdd);
-        acc_mx[q] = fma2(w1_6, sub(prev.zx[q], cur.jx[q]), add(t_mx[q], Smx));
-        acc_my[q] = fma2(half, sub(prev.zy[q], cur.jy[q]), t_my[q]);
+        acc_mx[q] = fma2(w1_6, sub(prev.zx[q], cur.zx[q]), add(t_mx[q], Smx));
+        acc_my[q] = fma2(half, sub(prev.zy[q], cur.zy[q]), t_my[q]);
         t_dd[q] = add(U, V);
         t_mx[q] = add(Up, Vp);
         t_my[q] = add(Y, U);
       }
+      if constexpr (kReduce)
+        rs_mass += static_cast<double>(mrow.x) + static_cast<double>(mrow.y);
       if (owner && out_row) {
         T *dd = static_cast<T *>(a.dst.d);
         T *dx = static_cast<T *>(a.dst.jx);
@@ -849,12 +995,11 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
           if (a.sr) {  // uniform across the warp
             stored = true;
             const uint32_t xs = static_cast<uint32_t>(xb);
-            // one key per (row, step); fields offset it by constants
+            // one key per (row, step)
             const uint32_t key =
                 fmix32(fmix32(a.step) ^ (static_cast<uint32_t>(o) * 0x85ebca77u));
-            store_pairs_sr<kC, T>(dd + off, od, SS::kD, key, xs);
-            store_pairs_sr<kC, T>(dx + off, ox, SS::kJ, key + 0x632be5abu, xs);
-            store_pairs_sr<kC, T>(dy + off, oy, SS::kJ, key + 0xc6bc279au, xs);
+            store_row_sr<kC, T>(dd + off, dx + off, dy + off, od, ox, oy, key,
+                                xs);
           }
         }
         if (!stored) {
@@ -867,38 +1012,81 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
       pS6 = S6;
     };
 
-    int issued = 0;
+    // Ring rows are taken in order, so the stage and phase parity of the
+    // next row to take (tst, tph) and the stage of the next row to issue
+    // (ist) advance by one per row instead of being divided out.
+    int issued = 0, ist = 0, tst = 0;
+    unsigned tph = 0u;
     if (lane == 0) {
       for (int st = 0; st < kS; ++st) mbar_init(bars + st);
       fence_async_shared();
-      for (; issued < nrows && issued < kS; ++issued) issue(issued);
+      for (; issued < nrows && issued < kS; ++issued) issue(issued, issued);
     }
     issued = __shfl_sync(kFull, issued, 0);
+    ist = issued == kS ? 0 : issued;
     __syncwarp();
     // takes ring row i into `r` and refills its stage; false on a timeout
     auto take = [&](int i, Row &r) -> bool {
-      const bool ok = fetch(i, r);
+      const bool ok = fetch(i, tst, tph, r);
       if (!__all_sync(kFull, ok)) return false;
       __syncwarp();  // every lane has read the stage
-      if (lane == 0 && issued < nrows) {
-        fence_async_shared();
-        issue(issued);
+      if (issued < nrows) {
+        if (lane == 0) {
+          fence_async_shared();
+          issue(issued, ist);
+        }
+        ++issued;
+        ist = ist + 1 == kS ? 0 : ist + 1;
       }
-      issued = min(issued + 1, nrows);
+      if (++tst == kS) {
+        tst = 0;
+        tph ^= 1u;
+      }
       return true;
     };
+    // reads the next ring row i (the one after the last taken) into `r`
+    // without releasing its stage (kSC: the row above the source row being
+    // taken); false on a timeout
+    auto peek = [&](int i, Row &r) -> bool {
+      return __all_sync(kFull, fetch(i, tst, tph, r));
+    };
     int failed = -1;
-    for (int k = 0; k < npairs; ++k) {
-      if (!take(2 * k, ra)) {
-        failed = 2 * k;
+    // potential terms of two rows (kSC), swapping roles row by row
+    float2 tC0[kP], tA0[kP], tS0[kP], tC1[kP], tA1[kP], tS1[kP];
+    Row rn;  // kSC: the row above the current source row
+    if constexpr (kSC) {
+      // the row below the first source row and the first source row itself
+      if (!take(0, rb)) {
+        failed = 0;
+      } else if (!peek(1, rn)) {
+        failed = 1;
+      } else {
+        psi_terms(rb, tC0, tA0, tS0);
+        psi_terms(rn, tC1, tA1, tS1);
+#pragma unroll
+        for (int q = 0; q < kP; ++q) rb.zx[q] = rb.zy[q] = bc(0.f);
+      }
+    }
+    for (int k = 0; k < npairs && failed < 0; ++k) {
+      const int r0 = 2 * k + kLead;  // ring row of source row 2k
+      if (!take(r0, ra)) {
+        failed = r0;
         break;
       }
-      row(2 * k, ra, rb);
-      if (!take(2 * k + 1, rb)) {
-        failed = 2 * k + 1;
+      if (kSC && !peek(r0 + 1, rn)) {
+        failed = r0 + 1;
         break;
       }
-      row(2 * k + 1, rb, ra);
+      row(2 * k, ra, rb, rn, tC0, tA0, tS0, tC1, tA1, tS1);
+      if (!take(r0 + 1, rb)) {
+        failed = r0 + 1;
+        break;
+      }
+      if (kSC && !peek(r0 + 2, rn)) {
+        failed = r0 + 2;
+        break;
+      }
+      row(2 * k + 1, rb, ra, rn, tC1, tA1, tS1, tC0, tA0, tS0);
     }
     if (failed >= 0) {
       if (lane == 0) atomicOr(a.flag, kFlagCopyTimeout);
@@ -919,7 +1107,7 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
   if constexpr (kReduce) {
     double v0 = static_cast<double>(rs_num.x) + rs_num.y;
     double v1 = static_cast<double>(rs_den.x) + rs_den.y;
-    double v2 = static_cast<double>(rs_mass.x) + rs_mass.y;
+    double v2 = rs_mass;
 #pragma unroll
     for (int o = kLanes / 2; o > 0; o >>= 1) {
       v0 += __shfl_xor_sync(kFull, v0, o);
@@ -942,14 +1130,15 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
 // Runs warp tile (bx, by, w).  kDual: with the code for clean tiles when
 // the tile's flag says so (flags absent: the general code); otherwise the
 // general code only, which keeps the kernel's registers for one code path.
-template <typename T, int kC, int kRows, int kS, bool kReduce, bool kDual>
+template <typename T, int kC, int kRows, int kS, bool kReduce, bool kDual,
+          bool kSC = false>
 __device__ __forceinline__ void run_tile(const StepLaunch &a, int64_t bx,
                                          int64_t by, int w, int slot,
                                          int64_t gx, const SolidSums *lut,
                                          unsigned char *smem) {
   if constexpr (!kDual) {
-    step_tile<T, kC, kRows, kS, kReduce, false>(a, bx, by, w, slot, gx, lut,
-                                                smem);
+    step_tile<T, kC, kRows, kS, kReduce, false, kSC>(a, bx, by, w, slot, gx,
+                                                     lut, smem);
     return;
   }
   const bool clean = a.clean && a.clean[(by * gx + bx) * kWarps + w];
@@ -961,17 +1150,20 @@ __device__ __forceinline__ void run_tile(const StepLaunch &a, int64_t bx,
                                                 smem);
 }
 
+// kSC: the Shan-Chen multiphase step (general tile code only: the clean-tile
+// test does not cover the extra rows its force needs).
 template <typename T, int kC, int kRows, int kMinBlocks, int kS, bool kReduce,
-          bool kDual>
+          bool kDual, bool kSC = false>
 __global__ void __launch_bounds__(kThreads, kMinBlocks)
     lbm_step_kernel(const StepLaunch a) {
+  static_assert(!(kDual && kSC), "the multiphase step has no clean-tile code");
   extern __shared__ __align__(128) unsigned char smem[];
   SolidSums *lut = reinterpret_cast<SolidSums *>(smem);
   build_solid_lut(lut);
   __syncthreads();
   const int warp = threadIdx.x / kLanes;
-  run_tile<T, kC, kRows, kS, kReduce, kDual>(a, blockIdx.x, blockIdx.y, warp,
-                                             warp, gridDim.x, lut, smem);
+  run_tile<T, kC, kRows, kS, kReduce, kDual, kSC>(
+      a, blockIdx.x, blockIdx.y, warp, warp, gridDim.x, lut, smem);
 }
 
 // Batched step: a persistent grid whose warps take warp tiles of many domains
@@ -1073,6 +1265,47 @@ __global__ void unpack_kernel(Fields f, const uint8_t *__restrict__ mask,
   }
 }
 
+// The change of the velocity field since a snapshot: per warp, the FP64
+// sums of |u_now - u_snap|^2 and |u_now|^2 over fluid nodes (u = j / rho
+// decoded from either copy), written as the first two of its partial triple
+// (4 warps per block: the layout finalize_kernel sums).
+template <typename T>
+__global__ void __launch_bounds__(128)
+    change_kernel(Fields now, Fields snap, const uint8_t *__restrict__ mask,
+                  int64_t nx, int64_t ny, int64_t pitch,
+                  double *__restrict__ partials) {
+  using S = Storage<T>;
+  double s0 = 0.0, s1 = 0.0;
+  const int64_t n = nx * ny;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+       i < n; i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t o = (i / nx) * pitch + i % nx;
+    if (mask[o] != 0u) continue;
+    auto u_of = [&](const Fields &f, double &ux, double &uy) {
+      const double rho =
+          1.0 + S::decode(static_cast<const T *>(f.d)[o]) * (1.0 / S::kD);
+      ux = S::decode(static_cast<const T *>(f.jx)[o]) * (1.0 / S::kJ) / rho;
+      uy = S::decode(static_cast<const T *>(f.jy)[o]) * (1.0 / S::kJ) / rho;
+    };
+    double ax, ay, bx, by;
+    u_of(now, ax, ay);
+    u_of(snap, bx, by);
+    s0 += (ax - bx) * (ax - bx) + (ay - by) * (ay - by);
+    s1 += ax * ax + ay * ay;
+  }
+#pragma unroll
+  for (int m = kLanes / 2; m > 0; m >>= 1) {
+    s0 += __shfl_xor_sync(kFull, s0, m);
+    s1 += __shfl_xor_sync(kFull, s1, m);
+  }
+  if ((threadIdx.x & (kLanes - 1)) == 0) {
+    double *q = partials + 3 * (blockIdx.x * 4 + threadIdx.x / kLanes);
+    q[0] = s0;
+    q[1] = s1;
+    q[2] = 0.0;
+  }
+}
+
 // Writes the solid-node storage values rho - 1 = 0, j = -F.
 template <typename T>
 __global__ void solid_storage_kernel(Fields f, const uint8_t *__restrict__ mask,
@@ -1095,10 +1328,8 @@ struct Variant {
   bool dual;  // also carries the clean-tile code (flags per warp tile)
 };
 constexpr Variant kVariants[] = {
-    {4, 64, 2, 8, false}, {2, 64, 3, 12, false}, {4, 32, 2, 8, false},
-    {2, 64, 4, 10, false}, {4, 8, 2, 8, false},  {2, 8, 3, 12, false},
-    {4, 64, 2, 8, true},  {4, 64, 3, 6, false},  {4, 64, 3, 6, true},
-    {4, 8, 3, 6, false}};
+    {4, 64, 3, 6, false}, {4, 32, 3, 6, false}, {4, 16, 3, 6, false},
+    {4, 8, 3, 6, false},  {4, 64, 3, 6, true}};
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
 // Calls f(std::integral_constant<int, v>) for a run-time variant index v
@@ -1138,19 +1369,28 @@ dim3 step_grid(int64_t nx, int64_t ny, int vi) {
   return dim3(static_cast<unsigned>(gx), static_cast<unsigned>(gy), 1);
 }
 
-template <typename T, int kV, bool kReduce>
-cudaError_t launch_variant(const StepLaunch &a, dim3 g, cudaStream_t s) {
+template <typename T, int kV, bool kReduce, bool kSC>
+cudaError_t launch_kernel(const StepLaunch &a, dim3 g, cudaStream_t s) {
   constexpr Variant v = kVariants[kV];
   constexpr int smem = smem_bytes<T, v.cols, v.stages>();
   static_assert(smem <= 227 * 1024, "shared memory per block");
-  auto kern =
-      lbm_step_kernel<T, v.cols, v.rows, v.min_blocks, v.stages, kReduce, v.dual>;
+  auto kern = lbm_step_kernel<T, v.cols, v.rows, v.min_blocks, v.stages,
+                              kReduce, v.dual && !kSC, kSC>;
   static cudaError_t attr = cudaFuncSetAttribute(
       kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (attr != cudaSuccess) return attr;
   (void)cudaGetLastError();  // an earlier, unrelated non-sticky error
   kern<<<g, kThreads, smem, s>>>(a);
   return cudaGetLastError();
+}
+
+// The variant's kernel; a nonzero multiphase coupling (FP32 storage only)
+// takes the multiphase kernel of the same tile shape.
+template <typename T, int kV, bool kReduce>
+cudaError_t launch_variant(const StepLaunch &a, dim3 g, cudaStream_t s) {
+  if constexpr (std::is_same<T, float>::value)
+    if (a.g_sc != 0.0f) return launch_kernel<T, kV, kReduce, true>(a, g, s);
+  return launch_kernel<T, kV, kReduce, false>(a, g, s);
 }
 
 template <typename T, bool kReduce>
@@ -1187,18 +1427,17 @@ int occupancy(int v) {
 }
 
 // Picks the variant with the shortest expected step time for an nx x ny
-// domain.  The model, fitted to step times measured on a GB300 over the
-// 256^2 .. 16384^2 cavity sweep: blocks are spread evenly over the SMs, so the
-// busiest SM runs ceil(blocks / SMs) of them; one block marches kRows + 2
-// source rows per warp, each costing its columns per lane (two columns per
-// lane cost 1.215 times as much per column as four: fewer loads in flight per
-// instruction); and an SM that holds two or more blocks at once gets through
-// them 1.3 times as fast as one block alone (the kernel is issue-bound, so a
-// second block adds little and a third nothing measurable).
+// domain.  The model, fitted to step times measured on a GB300 (periodic
+// boxes and cavities, 1024^2 .. 16384^2): blocks are spread evenly over the
+// SMs, so the busiest SM runs ceil(blocks / SMs) of them, up to the kernel's
+// occupancy at a time; one block costs the kRows + 2 source rows each of its
+// warps marches; and k blocks resident together get through their rows
+// kConcurrent[k] times as fast as one block alone (the kernel is issue- and
+// latency-bound: more resident warps hide more latency).  A last, partial
+// round of blocks runs at its own, lower rate.
 template <typename T>
 int choose_variant_t(int64_t nx, int64_t ny) {
-  constexpr double kTwoColumnCost = 1.215;
-  constexpr double kSharedSpeedup = 1.3;
+  constexpr double kConcurrent[] = {1.0, 1.0, 1.3, 1.58};
   static int sms = [] {
     int dev = 0, n = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -1212,16 +1451,18 @@ int choose_variant_t(int64_t nx, int64_t ny) {
   double best_time = 0.0;
   for (int i = 0; i < kNumVariants; ++i) {
     const Variant v = kVariants[i];
+    if (v.dual) continue;  // chosen only through dual_variant, by its flags
     const int occ = occupancy<T>(i);
     if (occ <= 0) continue;
     const dim3 g = step_grid(nx, ny, i);
     const int64_t blocks = static_cast<int64_t>(g.x) * g.y;
     const int64_t per_sm = (blocks + sms - 1) / sms;
-    const double block_time =
-        (v.rows + 2.0) * v.cols * (v.cols == 2 ? kTwoColumnCost : 1.0);
-    const double rate = (occ >= 2 && per_sm >= 2) ? kSharedSpeedup : 1.0;
-    if (v.dual) continue;  // chosen only through dual_variant, by its flags
-    const double t = static_cast<double>(per_sm) * block_time / rate;
+    const int64_t k = occ < 3 ? occ : 3;
+    const int64_t full = per_sm / k, rest = per_sm % k;
+    const double t = (v.rows + 2.0) * (static_cast<double>(full * k) /
+                                           kConcurrent[k] +
+                                       static_cast<double>(rest) /
+                                           kConcurrent[rest]);
     if (best_time == 0.0 || t < best_time * (1.0 - 1e-9)) {
       best_time = t;
       best = i;
@@ -1308,11 +1549,22 @@ cudaError_t solid_t(Fields f, const uint8_t *mask, int64_t n, float fx,
   return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t change_t(Fields now, Fields snap, const uint8_t *mask, int64_t nx,
+                     int64_t ny, int64_t pitch, double *partials,
+                     int64_t blocks, cudaStream_t s) {
+  (void)cudaGetLastError();
+  change_kernel<T><<<static_cast<unsigned>(blocks), 128, 0, s>>>(
+      now, snap, mask, nx, ny, pitch, partials);
+  return cudaGetLastError();
+}
+
 // The launchers of storage type T, as the table lbm_step.cu dispatches on.
 template <typename T>
 constexpr StorageOps make_ops() {
   return StorageOps{&launch_step_t<T>, &launch_batch_t<T>, &choose_variant_t<T>,
-                    &pack_t<T>, &unpack_t<T>, &solid_t<T>};
+                    &pack_t<T>,        &unpack_t<T>,       &solid_t<T>,
+                    &change_t<T>};
 }
 
 }  // namespace

@@ -183,11 +183,10 @@ int dual_variant(int v, int64_t nx, int64_t ny) {
       n = 0;
     return n;
   }();
-  // the clean-tile code pays off only over many waves of blocks (measured:
-  // +2 to +14 % from 8192^2 up, a few per cent slower at 4096^2 and below,
-  // where the edge tiles' general code, which the dual kernel runs with
-  // fewer free registers, sets the step time)
-  if (sms <= 0 || launched_blocks(nx, ny, v) < 8 * static_cast<int64_t>(sms))
+  // the clean-tile code pays off once every SM runs a few blocks (measured:
+  // +2 % on a periodic 4096^2 box, +12 to +19 % on 8192^2 and 16384^2
+  // cavities, three blocks per SM)
+  if (sms <= 0 || launched_blocks(nx, ny, v) < 2 * static_cast<int64_t>(sms))
     return -1;
   for (int i = 0; i < kNumVariants; ++i) {
     const Variant d = kVariants[i];
@@ -246,6 +245,14 @@ cudaError_t launch_unpack(int storage, Fields f, const uint8_t *mask,
                           double *staging, int64_t nx, int64_t pitch,
                           int64_t y0, int64_t rows, cudaStream_t s) {
   return ops(storage).unpack(f, mask, staging, nx, pitch, y0, rows, s);
+}
+
+cudaError_t launch_change(int storage, Fields now, Fields snap,
+                          const uint8_t *mask, int64_t nx, int64_t ny,
+                          int64_t pitch, double *partials, int64_t blocks,
+                          cudaStream_t s) {
+  return ops(storage).change(now, snap, mask, nx, ny, pitch, partials, blocks,
+                             s);
 }
 
 cudaError_t launch_solid_storage(int storage, Fields f, const uint8_t *mask,

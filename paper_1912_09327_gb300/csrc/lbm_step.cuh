@@ -44,6 +44,9 @@ struct StepLaunch {
   // kFlagCopyTimeout); 0 gives up at once.  Draining the copies still in
   // flight before a warp leaves its tile always keeps the one-second bound.
   unsigned long long wait_ns = 1000000000ull;
+  // Shan-Chen coupling g of the multiphase step (0: single phase; FP32
+  // storage only)
+  float g_sc = 0.0f;
 };
 
 // One member of a batch (see launch_batch): both field copies, the copy that
@@ -94,6 +97,9 @@ struct StorageOps {
                         cudaStream_t s);
   cudaError_t (*solid)(Fields f, const uint8_t *mask, int64_t n, float fx,
                        float fy, cudaStream_t s);
+  cudaError_t (*change)(Fields now, Fields snap, const uint8_t *mask,
+                        int64_t nx, int64_t ny, int64_t pitch,
+                        double *partials, int64_t blocks, cudaStream_t s);
 };
 extern const StorageOps kOpsF32, kOpsF16, kOpsBF16;
 
@@ -158,6 +164,13 @@ cudaError_t launch_pack(int storage, const double *staging, Fields f,
 cudaError_t launch_unpack(int storage, Fields f, const uint8_t *mask,
                           double *staging, int64_t nx, int64_t pitch,
                           int64_t y0, int64_t rows, cudaStream_t s);
+
+// Sums |u_now - u_snap|^2 and |u_now|^2 over the fluid nodes into `blocks`
+// blocks of four partial triples (finalize them with launch_finalize).
+cudaError_t launch_change(int storage, Fields now, Fields snap,
+                          const uint8_t *mask, int64_t nx, int64_t ny,
+                          int64_t pitch, double *partials, int64_t blocks,
+                          cudaStream_t s);
 
 // Storage convention of the step kernel: a solid node holds rho - 1 = 0 and
 // j = -F (what a solid source contributes, with no test of the node type).

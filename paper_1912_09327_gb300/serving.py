@@ -108,17 +108,29 @@ class Server:
         self.chunk = int(chunk)
         self.tol = float(residual_tol)
         self.max_steps = int(max_steps)
-        free, _ = torch.cuda.mem_get_info()
-        self.budget = int(hbm_budget) if hbm_budget else int(0.8 * free)
+        # a fixed budget when given; else each admission asks the device
+        # how much memory is free at that moment (free_bytes)
+        self.budget = int(hbm_budget) if hbm_budget else None
+        self.reserve = 1 << 30  # kept free for the rest of the process
         self.keep_states = keep_states
         self.policy = policy
         self.max_nodes = int(max_active_nodes) if max_active_nodes else None
         self.max_wait = float(max_wait)
         self.auto_variant = True
 
-    def run(self, requests, clock=time.perf_counter):
+    def free_bytes(self):
+        """Device memory a new request may take now: what the driver
+        reports free plus what PyTorch's caching allocator holds unused,
+        less a reserve."""
+        torch = self.torch
+        free, _ = torch.cuda.mem_get_info()
+        cached = torch.cuda.memory_reserved() - torch.cuda.memory_allocated()
+        return free + cached - self.reserve
+
+    def run(self, requests, clock=time.perf_counter, on_done=None):
         """Serves `requests` (with arrival times in seconds from now);
-        returns one Result per request, in request order."""
+        returns one Result per request, in request order.  `on_done`, if
+        given, is called with each Result as its request completes."""
         pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
         waiting = []
         active = {}  # slot -> [req, dom, steps, admitted, bytes]
@@ -135,7 +147,9 @@ class Server:
                 req = select_next(waiting, now, self.policy, self.max_wait)
                 need = _footprint(req)
                 size = req.nx * req.ny
-                if active and (used + need > self.budget or
+                fits = (used + need <= self.budget if self.budget is not None
+                        else need <= self.free_bytes())
+                if active and (not fits or
                                (self.max_nodes is not None and
                                 nodes + size > self.max_nodes)):
                     break  # wait for memory or node budget to free up
@@ -172,6 +186,8 @@ class Server:
                     done[req.rid] = Result(req.rid, req.arrival, entry[3], t,
                                            steps, float(res[slot]), converged,
                                            req.nx * req.ny, state)
+                    if on_done is not None:
+                        on_done(done[req.rid])
                     self.batch.remove(slot)
                     dom.close()
                     used -= entry[4]
@@ -185,7 +201,7 @@ class Server:
 
 
 def serve_sequential(requests, chunk=200, residual_tol=1e-7, max_steps=20000,
-                     clock=time.perf_counter, keep_states=False):
+                     clock=time.perf_counter, keep_states=False, on_done=None):
     """The plain form: one request at a time, in arrival order."""
     import torch
     stream = torch.cuda.Stream()
@@ -210,6 +226,8 @@ def serve_sequential(requests, chunk=200, residual_tol=1e-7, max_steps=20000,
         out[req.rid] = Result(req.rid, req.arrival, admitted, clock() - t0,
                               steps, float(res), res <= residual_tol,
                               req.nx * req.ny, state)
+        if on_done is not None:
+            on_done(out[req.rid])
         dom.close()
     return [out[r.rid] for r in requests]
 

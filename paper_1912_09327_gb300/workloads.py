@@ -228,3 +228,39 @@ def request_stream(count: int, rate: float = 200.0, seed: int = 0,
         ny = _log_uniform_side(rng, lo, hi)
         out.append(Request(i, t, kind, nx, ny, seed * 100003 + i))
     return out
+
+
+def drop(n: int = 1024, g: float = -5.0, radius: float | None = None,
+         rho_l: float = 2.0, rho_g: float = 0.15, width: float = 2.0,
+         ny: int | None = None) -> Problem:
+    """The multiphase test of Section 4: a drop of liquid in a periodic box
+    of its vapour, at rest, for the Shan-Chen step with coupling g.  The
+    density is a smoothed disc (tanh profile of the given width) of radius
+    n/4 by default; rho_l and rho_g are near the coexistence densities of
+    g = -5, which the flow then settles to."""
+    ny = n if ny is None else ny
+    r = min(n, ny) / 4.0 if radius is None else radius
+    y, x = np.mgrid[0:ny, 0:n]
+    dist = np.hypot(x - (n - 1) / 2.0, y - (ny - 1) / 2.0)
+    rho = rho_g + 0.5 * (rho_l - rho_g) * (1.0 - np.tanh((dist - r) / width))
+    mask = np.zeros((ny, n), np.uint8)
+    z = np.zeros((ny, n))
+    return Problem("drop", mask, (True, True), (0.0, 0.0), rho, z, z.copy(),
+                   {"sc_g": g, "radius": r})
+
+
+def multiphase_random(nx: int, ny: int, seed: int = 0, g: float = -5.0,
+                      lo: float = 0.85, hi: float = 1.15, amp: float = 0.01,
+                      p_solid: float = 0.1, p_fixed: float = 0.03,
+                      periodic=(True, True), force=(1e-4, -5e-5)) -> Problem:
+    """Random node types and a random density in [lo, hi] with small random
+    momentum: the general parity case of the multiphase step."""
+    rng = np.random.default_rng(seed)
+    mask = random_mask((ny, nx), seed, p_solid, p_fixed)
+    rho = rng.uniform(lo, hi, (ny, nx))
+    jx = amp * rng.standard_normal((ny, nx))
+    jy = amp * rng.standard_normal((ny, nx))
+    solid = mask == SOLID
+    rho[solid], jx[solid], jy[solid] = 1.0, 0.0, 0.0
+    return Problem("multiphase_random", mask, tuple(periodic), tuple(force),
+                   rho, jx, jy, {"sc_g": g})

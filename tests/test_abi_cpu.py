@@ -60,7 +60,9 @@ def test_workspace_follows_storage_model(b):
 
 @pytest.mark.parametrize("bad", [dict(nx=0), dict(ny=0), dict(nx=-3),
                                  dict(storage=7), dict(rounding=3), dict(rounding=-1),
-                                 dict(fx=float("nan"))])
+                                 dict(fx=float("nan")), dict(sc_g=float("inf")),
+                                 dict(sc_g=-5.0, storage=1),
+                                 dict(sc_g=-5.0, storage=2)])
 def test_invalid_params(b, bad):
     p = b.make_params(10, 10)
     for k, v in bad.items():

@@ -223,13 +223,32 @@ def test_batch_mix512_sample_matches_oracle(b):
     batch.step(2000)
     res, _, status = batch.residuals()
     assert all(s == b.LBM_OK for s in status[: len(doms)])
-    for i in pick:
-        p = probs[i]
-        g = doms[i].moments()
-        o = oracle.run(p.mask, *p.state(), 2000, p.periodic, p.force)
-        err = velocity_error(g, o)
-        assert err <= 1e-5, (i, p.name, p.mask.shape, err)
-        assert np.abs(g[0] - o[0]).max() <= 1e-5, (i, p.name)
+    got = {i: doms[i].moments() for i in pick}
     batch.close()
     for d in doms:
         d.close()
+    # the same mix in 16-bit storage (stochastic rounding)
+    got16 = {}
+    for fmt in ("f16", "bf16"):
+        doms = [b.Domain.from_problem(p, stream=stream, storage=fmt)
+                for p in probs]
+        batch = b.Batch(len(doms), tiles, stream=stream)
+        for d in doms:
+            batch.add(d)
+        batch.step(2000)
+        got16[fmt] = {i: doms[i].moments() for i in pick}
+        batch.close()
+        for d in doms:
+            d.close()
+    worst = {"f16": 0.0, "bf16": 0.0}
+    for i in pick:
+        p = probs[i]
+        o = oracle.run(p.mask, *p.state(), 2000, p.periodic, p.force)
+        g = got[i]
+        err = velocity_error(g, o)
+        assert err <= 1e-5, (i, p.name, p.mask.shape, err)
+        assert np.abs(g[0] - o[0]).max() <= 1e-5, (i, p.name)
+        for fmt in worst:
+            worst[fmt] = max(worst[fmt], velocity_error(got16[fmt][i], o))
+    print("batch mix sample x 2000, worst max|du|/max|u|:", worst)
+    assert worst["f16"] <= 4e-3 and worst["bf16"] <= 4e-2, worst

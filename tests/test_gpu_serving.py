@@ -66,3 +66,28 @@ def test_service_summary_and_sequential_form(mods):
     s = serving.summary(batched)
     assert s["requests"] == 8 and s["p99_latency_s"] >= s["p50_latency_s"] > 0
     assert s["converged"] + s["capped"] == 8
+
+
+def test_served_result_matches_oracle(mods):
+    """A request taken from a served mix (a channel, a cavity and a porous
+    sample arriving while others run) against the FP64 oracle run for the
+    same number of steps: the spec velocity bound."""
+    import oracle
+    binding, serving = mods
+    reqs = [wl.Request(0, 0.00, "porous", 180, 150, 11),
+            wl.Request(1, 0.01, "channel", 96, 40, 12),
+            wl.Request(2, 0.02, "cavity", 70, 64, 13)]
+    srv = serving.Server(capacity=4, chunk=200, residual_tol=1e-7,
+                         max_steps=4000, keep_states=True)
+    results = srv.run(reqs)
+    srv.close()
+    oracle.set_threads(oracle.max_threads())
+    for q, r in zip(reqs, results):
+        p = q.problem()
+        o = oracle.run(p.mask, *p.state(), r.steps, p.periodic, p.force)
+        d, jx, jy = (x.astype(np.float64) for x in r.state)
+        rho = 1.0 + d
+        keep = p.mask != wl.SOLID
+        u = np.stack([jx / rho, jy / rho])[:, keep]
+        uo = np.stack([o[1] / o[0], o[2] / o[0]])[:, keep]
+        assert np.abs(u - uo).max() <= 1e-5 * np.abs(uo).max(), q.kind

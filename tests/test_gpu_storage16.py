@@ -170,3 +170,27 @@ def test_stochastic_rounding_is_reproducible_and_resumable(b, fmt):
     e.close()
     for x, y in zip(resumed, runs[0]):
         assert np.array_equal(x.view(np.uint16), y.view(np.uint16))
+
+
+def test_change_since_snapshot(b):
+    """The span change (lbm_snapshot / lbm_change_since) is the FP64 mean
+    relative velocity change per step, as computed on the host from the two
+    states; on the FP16 channel at its steady state the per-step residual
+    sits at the rounding noise while the change over 10000 steps falls two
+    orders below it, so a 16-bit solve has a convergence test that fires."""
+    p = wl.channel(64, 32, 0.01)
+    d = b.Domain.from_problem(p, storage="f16")
+    d.step(20000)
+    res, _ = d.residual()
+    snap = d.snapshot()
+    R0, U0, V0 = d.moments()
+    d.step(10000)
+    ch = d.change_since(snap, 10000)
+    R1, U1, V1 = d.moments()
+    d.close()
+    fluid = p.mask == 0
+    num = (((U1 / R1 - U0 / R0) ** 2 + (V1 / R1 - V0 / R0) ** 2)[fluid]).sum()
+    den = (((U1 / R1) ** 2 + (V1 / R1) ** 2)[fluid]).sum()
+    assert ch == pytest.approx(np.sqrt(num / den) / 10000, rel=1e-6)
+    assert res > 1e-4              # the per-step residual: rounding noise
+    assert ch < res / 100          # the span change: below it by far

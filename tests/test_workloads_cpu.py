@@ -93,12 +93,13 @@ def test_serving_admission_order():
 
 def test_serving_batch_variant_model():
     """The service's tile variant for a batch: least padded tile work.  Many
-    64 x 64 domains fit short 8-row warp tiles; one 4096^2 domain wastes
-    little in the tall default tiles, which march fewer halo rows."""
+    64 x 64 domains fit the 16-row warp tiles (one 120 x 64 block tile each);
+    one 4096^2 domain wastes little in the tall default tiles, which march
+    fewer halo rows."""
     from paper_1912_09327_gb300 import binding, serving
     small = serving.choose_batch_variant([(64, 64)] * 20)
     tx, ty, cols = binding.lbm_variant_tile(small)
-    assert ty == 32 and cols == 4
+    assert ty == 64 and cols == 4
     big = serving.choose_batch_variant([(4096, 4096)])
     assert binding.lbm_variant_tile(big)[1] == 256
     assert 0 <= serving.choose_batch_variant([(1, 1)]) < binding.lbm_variant_count()
