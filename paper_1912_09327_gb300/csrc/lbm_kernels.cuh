@@ -521,11 +521,13 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
   // FP32 storage with stochastic rounding: this step's dither
   const float2 dither = bc(kF32 && a.sr ? fp32_dither(a.step) : 0.0f);
 
-  // Residual sums in FP32 per lane; the mass in FP64, each row's FP32 sum of
-  // a lane's (at most four) nodes added to it: densities of order one (the
-  // multiphase step) keep their precision over a tile's rows.
+  // Residual sums in FP32 per lane (at most 64 rows x 4 columns of a tile),
+  // FP64 from the warp sums on: non-negative terms, a lane's rounding error a
+  // few 1e-6 of its own sum.  The mass is a compensated (Kahan) FP32 sum of
+  // the lane's row sums: deviations of order one (a multiphase vapour) keep
+  // it to about 1e-7 of a lane's sum.
   float2 rs_num = bc(0.f), rs_den = bc(0.f);
-  double rs_mass = 0.0;
+  float rs_mass = 0.f, rs_comp = 0.f;
   float rmin = 1.0f;
 
   if (y0 < a.ny) {
@@ -856,7 +858,7 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
       }
 
       float2 od[kP], ox[kP], oy[kP];
-      float2 mrow = bc(0.f);  // this row's mass terms (kReduce)
+      float mrow = 0.f;  // this row's mass terms (kReduce)
 #pragma unroll
       for (int q = 0; q < kP; ++q) {
         const float2 KL = Ks[q], KR = Ks[q + 1];
@@ -934,44 +936,38 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
           ox[q] = mxn;
           oy[q] = myn;
         }
-        if constexpr (kReduce) {
-          // u_new - u_old = ((j_n - j_o) - u_o (d_n - d_o)) / rho_n: the
-          // step's own changes, no cancellation between two O(|u|) values.
-          // u_o is taken as j_o / rho_n, which errs by the relative density
-          // change of the step in this second-order term only.
+        if constexpr (kReduce && !kClean) {
+          // The residual's terms.  u_new - u_old = ((j_n - j_o) -
+          // u_o (d_n - d_o)) / rho_n: the step's own changes, no cancellation
+          // between two O(|u|) values; u_o is taken as j_o / rho_n, which
+          // errs by the relative density change of the step in this
+          // second-order term only.  So (|u_n - u_o|^2, |u_n|^2) =
+          // (|e|^2, |j_n|^2) / rho_n^2 with e = (j_n - j_o) -
+          // j_o (d_n - d_o) / rho_n, the division by rho_n^2 folded into the
+          // accumulating FMAs.  Only valid nodes add (fluid, owned, in an
+          // output row).
           const float2 rn = add(dn, one);
           const float2 irn =
               make_float2(__fdividef(1.0f, rn.x), __fdividef(1.0f, rn.y));
           const float2 irn2 = mul(irn, irn);
-          const float2 mdd = sub(dO, dn);
-          const float2 ex = fma2(mul(jxO, irn), mdd, sub(mxn, jxO));
-          const float2 ey = fma2(mul(jyO, irn), mdd, sub(myn, jyO));
-          const float2 nn = mul(fma2(ex, ex, mul(ey, ey)), irn2);
-          const float2 dd2 = mul(fma2(mxn, mxn, mul(myn, myn)), irn2);
-          if constexpr (kClean) {
-            // a clean tile has every column in the domain and fluid: both
-            // nodes of a pair count exactly when the lane owns outputs
-            if (owner && out_row) {
-              rs_num = add(rs_num, nn);
-              rs_den = add(rs_den, dd2);
-              mrow = add(mrow, dn);
-              rmin = fminf(rmin, fminf(rn.x, rn.y));
-            }
-          } else {
-            const bool v0 = f0 && out_row && ((out_cols >> (2 * q)) & 1u);
-            const bool v1 = f1 && out_row && ((out_cols >> (2 * q + 1)) & 1u);
-            if (v0) {
-              rs_num.x += nn.x;
-              rs_den.x += dd2.x;
-              mrow.x += dn.x;
-              rmin = fminf(rmin, rn.x);
-            }
-            if (v1) {
-              rs_num.y += nn.y;
-              rs_den.y += dd2.y;
-              mrow.y += dn.y;
-              rmin = fminf(rmin, rn.y);
-            }
+          const float2 t = mul(sub(dO, dn), irn);
+          const float2 ex = fma2(jxO, t, sub(mxn, jxO));
+          const float2 ey = fma2(jyO, t, sub(myn, jyO));
+          const float2 nn = fma2(ex, ex, mul(ey, ey));
+          const float2 dd2 = fma2(mxn, mxn, mul(myn, myn));
+          const bool v0 = f0 && out_row && ((out_cols >> (2 * q)) & 1u);
+          const bool v1 = f1 && out_row && ((out_cols >> (2 * q + 1)) & 1u);
+          if (v0) {
+            rs_num.x = fmaf(nn.x, irn2.x, rs_num.x);
+            rs_den.x = fmaf(dd2.x, irn2.x, rs_den.x);
+            mrow += dn.x;
+            rmin = fminf(rmin, rn.x);
+          }
+          if (v1) {
+            rs_num.y = fmaf(nn.y, irn2.y, rs_num.y);
+            rs_den.y = fmaf(dd2.y, irn2.y, rs_den.y);
+            mrow += dn.y;
+            rmin = fminf(rmin, rn.y);
           }
         }
         // carry to output row s: South(s - 1) + Same(s) and the vertical
@@ -983,8 +979,40 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
         t_mx[q] = add(Up, Vp);
         t_my[q] = add(Y, U);
       }
-      if constexpr (kReduce)
-        rs_mass += static_cast<double>(mrow.x) + static_cast<double>(mrow.y);
+      if constexpr (kReduce && kClean) {
+        // The same terms as the general code's, in the same order; every
+        // lane sums its row (the halo lanes' sums are dropped at the end of
+        // the tile), as one block after the row's arithmetic.
+        if (out_row) {
+#pragma unroll
+          for (int q = 0; q < kP; ++q) {
+            const float2 dn = od[q], mxn = ox[q], myn = oy[q];
+            const float2 dO = prev.d[q], jxO = prev.jx[q], jyO = prev.jy[q];
+            const float2 rn = add(dn, one);
+            const float2 irn =
+                make_float2(__fdividef(1.0f, rn.x), __fdividef(1.0f, rn.y));
+            const float2 irn2 = mul(irn, irn);
+            const float2 t = mul(sub(dO, dn), irn);
+            const float2 ex = fma2(jxO, t, sub(mxn, jxO));
+            const float2 ey = fma2(jyO, t, sub(myn, jyO));
+            const float2 nn = fma2(ex, ex, mul(ey, ey));
+            const float2 dd2 = fma2(mxn, mxn, mul(myn, myn));
+            rs_num = fma2(nn, irn2, rs_num);
+            rs_den = fma2(dd2, irn2, rs_den);
+            mrow += dn.x;
+            mrow += dn.y;
+            rmin = fminf(rmin, fminf(rn.x, rn.y));
+          }
+        }
+      }
+      if constexpr (kReduce) {
+        if (out_row) {  // compensated sum of the rows (uniform branch)
+          const float y = __fsub_rn(mrow, rs_comp);
+          const float t = __fadd_rn(rs_mass, y);
+          rs_comp = __fsub_rn(__fsub_rn(t, rs_mass), y);
+          rs_mass = t;
+        }
+      }
       if (owner && out_row) {
         T *dd = static_cast<T *>(a.dst.d);
         T *dx = static_cast<T *>(a.dst.jx);
@@ -1105,9 +1133,14 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
   }
 
   if constexpr (kReduce) {
+    if (!owner) {  // a halo lane's sums (clean tiles add every lane's)
+      rs_num = rs_den = bc(0.f);
+      rs_mass = rs_comp = 0.f;
+      rmin = 1.0f;
+    }
     double v0 = static_cast<double>(rs_num.x) + rs_num.y;
     double v1 = static_cast<double>(rs_den.x) + rs_den.y;
-    double v2 = rs_mass;
+    double v2 = static_cast<double>(rs_mass) - rs_comp;
 #pragma unroll
     for (int o = kLanes / 2; o > 0; o >>= 1) {
       v0 += __shfl_xor_sync(kFull, v0, o);
