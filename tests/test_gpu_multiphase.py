@@ -92,8 +92,11 @@ def test_drop_128(binding):
         Ro, Uo, Vo = o
         u = np.stack([U / R, V / R])
         uo = np.stack([Uo / Ro, Vo / Ro])
-        assert np.abs(u - uo).max() <= bound_u * np.abs(uo).max(), n
-        assert np.abs(R - Ro).max() <= bound_r * Ro.max(), n
+        eu = np.abs(u - uo).max() / np.abs(uo).max()
+        er = np.abs(R - Ro).max() / Ro.max()
+        print("drop 128^2 x %d: velocity %.3g, density %.3g" % (n, eu, er))
+        assert eu <= bound_u, n
+        assert er <= bound_r, n
     # mass, conserved on the periodic domain: the FP32 state keeps it to
     # 5e-6 over 2000 steps (measured 1.8e-6; the drop is quasi-static, so its
     # rounding errors repeat each step instead of cancelling)
