@@ -756,13 +756,13 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
       }
       const float hm = __shfl_up_sync(kFull, C[kP - 1].y, 1);
       const float hp = __shfl_down_sync(kFull, C[0].x, 1);
+      // column by column, as for the row's other neighbour terms
 #pragma unroll
       for (int q = 0; q < kP; ++q) {
-        const float2 L = make_float2(q == 0 ? hm : C[q - 1].y, C[q].x);
-        const float2 R =
-            make_float2(C[q].y, q == kP - 1 ? hp : C[q + 1].x);
-        A[q] = sub(R, L);
-        S[q] = add(R, L);
+        const float l0 = q == 0 ? hm : C[q - 1].y, l1 = C[q].x;
+        const float r0 = C[q].y, r1 = q == kP - 1 ? hp : C[q + 1].x;
+        A[q] = make_float2(__fsub_rn(r0, l0), __fsub_rn(r1, l1));
+        S[q] = make_float2(__fadd_rn(r0, l0), __fadd_rn(r1, l1));
       }
     };
     // Source row s = ty0 - 1 + i, fetched into `cur`; `prev` holds row s - 1.
@@ -830,23 +830,20 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
         X[q] = mul(quarter, pxy);
         R0[q] = fma2(cm15, tr, dfj);
       }
-      // Left and right neighbours: sh[q] = (column 2q - 1, column 2q), so
-      // pair q's left neighbours are sh[q] and its right ones sh[q + 1];
-      // columns -1 and kC come from the neighbouring lanes.
-      auto shifted = [&](const float2 (&v)[kP], float2 (&sh)[kP + 1]) {
-        const float hm = __shfl_up_sync(kFull, v[kP - 1].y, 1);
-        const float hp = __shfl_down_sync(kFull, v[0].x, 1);
-        sh[0] = make_float2(hm, v[0].x);
-#pragma unroll
-        for (int q = 1; q < kP; ++q) sh[q] = make_float2(v[q - 1].y, v[q].x);
-        sh[kP] = make_float2(v[kP - 1].y, hp);
+      // Left and right neighbours: the columns -1 and kC of a row come from
+      // the neighbouring lanes; the sums and differences of a pair's left
+      // and right neighbours are formed column by column (scalar adds round
+      // as the packed ones do, and need no register moves to pair up
+      // neighbouring columns).
+      struct Halo {
+        float m, p;
       };
-      float2 Ks[kP + 1], Gsh[kP + 1], Xsh[kP + 1], Zx[kP + 1], Zy[kP + 1];
-      shifted(K, Ks);
-      shifted(G, Gsh);
-      shifted(X, Xsh);
-      shifted(cur.zx, Zx);
-      shifted(cur.zy, Zy);
+      auto halo = [&](const float2 (&v)[kP]) -> Halo {
+        return {__shfl_up_sync(kFull, v[kP - 1].y, 1),
+                __shfl_down_sync(kFull, v[0].x, 1)};
+      };
+      const Halo hK = halo(K), hG = halo(G), hX = halo(X);
+      const Halo hZx = halo(cur.zx), hZy = halo(cur.zy);
       unsigned S6 = 0u;
       bool any_solid = false;
       if constexpr (!kClean) {
@@ -861,17 +858,37 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
       float mrow = 0.f;  // this row's mass terms (kReduce)
 #pragma unroll
       for (int q = 0; q < kP; ++q) {
-        const float2 KL = Ks[q], KR = Ks[q + 1];
-        const float2 GL = Gsh[q], GR = Gsh[q + 1];
-        const float2 XL = Xsh[q], XR = Xsh[q + 1];
-        const float2 zxL = Zx[q], zxR = Zx[q + 1], zxC = cur.zx[q];
-        const float2 zyL = Zy[q], zyR = Zy[q + 1], zyC = cur.zy[q];
-        const float2 Gs = add(GL, GR), Gd = sub(GL, GR);
-        const float2 Xs = add(XL, XR), Xd = sub(XL, XR);
-        const float2 mxd = sub(zxL, zxR), myd = sub(zyL, zyR);
-        const float2 mys = add(add(zyL, zyR), F22y);
-        const float2 hx = add(sub(zxL, zxC), sub(zxR, zxC));  // exact
-        const float2 hy = add(sub(zyL, zyC), sub(zyR, zyC));
+        const float2 zxC = cur.zx[q], zyC = cur.zy[q];
+        // column j (-1 .. kC) of a row of pairs with its halo columns
+        auto col = [](const float2 (&v)[kP], const Halo &h, int j) -> float {
+          return j < 0 ? h.m : j >= kC ? h.p
+                                       : ((j & 1) ? v[j >> 1].y : v[j >> 1].x);
+        };
+        // the pair's left neighbours are columns 2q - 1, 2q and its right
+        // ones 2q + 1, 2q + 2: left + right, left - right, and the
+        // differences of a side with the pair itself
+        auto lpr = [&](const float2 (&v)[kP], const Halo &h) {
+          return make_float2(__fadd_rn(col(v, h, 2 * q - 1), col(v, h, 2 * q + 1)),
+                             __fadd_rn(col(v, h, 2 * q), col(v, h, 2 * q + 2)));
+        };
+        auto lmr = [&](const float2 (&v)[kP], const Halo &h) {
+          return make_float2(__fsub_rn(col(v, h, 2 * q - 1), col(v, h, 2 * q + 1)),
+                             __fsub_rn(col(v, h, 2 * q), col(v, h, 2 * q + 2)));
+        };
+        auto side = [&](const float2 (&v)[kP], const Halo &h, int j0,
+                        float2 c) {
+          return make_float2(__fsub_rn(col(v, h, j0), c.x),
+                             __fsub_rn(col(v, h, j0 + 1), c.y));
+        };
+        const float2 Ks = lpr(K, hK), Kd = lmr(K, hK);
+        const float2 Gs = lpr(G, hG), Gd = lmr(G, hG);
+        const float2 Xs = lpr(X, hX), Xd = lmr(X, hX);
+        const float2 mxd = lmr(cur.zx, hZx), myd = lmr(cur.zy, hZy);
+        const float2 mys = add(lpr(cur.zy, hZy), F22y);
+        const float2 hx = add(side(cur.zx, hZx, 2 * q - 1, zxC),  // exact
+                              side(cur.zx, hZx, 2 * q + 1, zxC));
+        const float2 hy = add(side(cur.zy, hZy, 2 * q - 1, zyC),
+                              side(cur.zy, hZy, 2 * q + 1, zyC));
         // Row s as the row above output row s - 1 (N: NW, N, NE) and below
         // output row s + 1 (T: SW, S, SE).  The two share their terms up to
         // signs:
@@ -884,8 +901,8 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
         const float2 Y = fma2(w1_12, hy, Xd);
         const float2 Up = fma2(w1_12, hx, Gd), Vp = fma2(w1_12, myd, Xs);
         // Row s as the own row of output row s (W, O, E)
-        const float2 Sdd = fma2(w4_9, R0[q], fma2(w1_3, mxd, add(KL, KR)));
-        const float2 Smx = fma2(w1_3, hx, sub(KL, KR));
+        const float2 Sdd = fma2(w4_9, R0[q], fma2(w1_3, mxd, Ks));
+        const float2 Smx = fma2(w1_3, hx, Kd);
 
         // Output row s - 1: the momentum in increment form on the base z_O
         // (j_O, plus F_SC(O) for the multiphase step), every z_P - z_O an
