@@ -75,12 +75,17 @@ def test_one_step_matches_oracle_to_format_rounding(b, fmt, nx, ny, per,
         assert np.all(np.abs(gg - ref)[fluid] <= tol[fluid])
 
 
+# Bounds: the measured errors with a margin (round to nearest is
+# deterministic; the stochastic rounding draws its bits from the step count,
+# so its errors repeat run to run too).  Measured, oracle / profile:
+# f32 4.6e-6 / 1.6e-3, f16 nearest 0.180 / 0.181, bf16 nearest 0.608 / 0.609,
+# f16 stochastic 1.3e-3 / 2.2e-3, bf16 stochastic 9.8e-3 / 5.9e-3.
 @pytest.mark.parametrize("fmt,rounding,oracle_bound,profile_bound",
                          [("f32", "nearest", 1e-5, 1e-2),
-                          ("f16", "nearest", 0.2, 0.25),
-                          ("bf16", "nearest", 1.0, 1.0),
-                          ("f16", "stochastic", 0.01, 0.02),
-                          ("bf16", "stochastic", 0.05, 0.05)])
+                          ("f16", "nearest", 0.2, 0.2),
+                          ("bf16", "nearest", 0.7, 0.7),
+                          ("f16", "stochastic", 4e-3, 5e-3),
+                          ("bf16", "stochastic", 3e-2, 2e-2)])
 def test_channel_error_report(b, fmt, rounding, oracle_bound, profile_bound):
     """Channel 64 x 32, 5000 steps: relative velocity error against the FP64
     oracle and against the analytic parabola u = 3 f y (H - y).  Round-to-
