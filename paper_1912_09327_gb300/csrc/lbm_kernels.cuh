@@ -437,6 +437,14 @@ __host__ __device__ constexpr int smem_bytes() {
          kWarps * ring_bytes<T, kC, kS>();
 }
 
+// The batched kernel's block adds one launch-state slot per warp after the
+// rings.
+template <typename T, int kC, int kS>
+__host__ __device__ constexpr int batch_smem_bytes() {
+  return smem_bytes<T, kC, kS>() +
+         kWarps * ((static_cast<int>(sizeof(StepLaunch)) + 15) / 16 * 16);
+}
+
 // The step kernel's warp tile.  kC columns per lane (4: 16-byte rows of
 // FP32, 2: 8-byte rows), kRows output rows per warp (even).  The warp marches
 // down its tile one source row s at a time; all per-node arithmetic runs on
@@ -1216,6 +1224,30 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks)
       a, blockIdx.x, blockIdx.y, warp, warp, gridDim.x, lut, smem);
 }
 
+// The launch state of batch member m for one step: copy c holds its state.
+__device__ __forceinline__ void fill_launch(StepLaunch &a, const BatchMember &m,
+                                            int c, int storage,
+                                            unsigned clock) {
+  StepLaunch t;  // the defaults (wait limit, single phase, ...) included
+  t.src = m.f[c];
+  t.dst = m.f[1 - c];
+  t.mask = m.mask;
+  t.nx = m.nx;
+  t.ny = m.ny;
+  t.pitch = m.pitch;
+  t.periodic_x = m.periodic_x;
+  t.periodic_y = m.periodic_y;
+  t.fx = m.fx;
+  t.fy = m.fy;
+  t.partials = m.partials;
+  t.flag = m.flag;
+  t.storage = storage;
+  t.sr = m.sr;
+  t.step = static_cast<uint32_t>(m.step_base) + clock;
+  t.clean = m.clean;
+  a = t;
+}
+
 // Batched step: a persistent grid whose warps take warp tiles of many domains
 // from one work list through an atomic counter, so that one launch advances
 // every member of a batch by one step.  Each warp works on its own (its own
@@ -1234,34 +1266,28 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks)
   __syncthreads();
   const int n = *b.nitems;
   const int slot = threadIdx.x / kLanes;
+  const bool lead = (threadIdx.x & (kLanes - 1)) == 0;
+  // The item's launch state lives in the warp's shared-memory slot, not in
+  // registers: the tile code reads its fields where it needs them, which
+  // keeps the kernel inside the register budget of three blocks per SM.
+  StepLaunch &a = reinterpret_cast<StepLaunch *>(
+      smem + smem_bytes<T, kC, kS>())[slot];
   for (;;) {
     int it = 0;
-    if ((threadIdx.x & (kLanes - 1)) == 0)
-      it = static_cast<int>(atomicAdd(b.counter, 1u));
+    if (lead) it = static_cast<int>(atomicAdd(b.counter, 1u));
     it = __shfl_sync(kFull, it, 0);
     if (it >= n) break;
-    const int4 w = b.items[it];  // member, tile x, tile y, warp
-    const BatchMember &m = b.members[w.x];
-    const int c = (m.cur ^ b.parity) & 1;
-    StepLaunch a;
-    a.src = m.f[c];
-    a.dst = m.f[1 - c];
-    a.mask = m.mask;
-    a.nx = m.nx;
-    a.ny = m.ny;
-    a.pitch = m.pitch;
-    a.periodic_x = m.periodic_x;
-    a.periodic_y = m.periodic_y;
-    a.fx = m.fx;
-    a.fy = m.fy;
-    a.partials = m.partials;
-    a.flag = m.flag;
-    a.storage = b.storage;
-    a.sr = m.sr;
-    a.step = static_cast<uint32_t>(m.step_base) + clock;
-    a.clean = m.clean;
-    run_tile<T, kC, kRows, kS, kReduce, kDual>(a, w.y, w.z, w.w, slot, m.gx,
-                                               lut, smem);
+    __syncwarp();  // every lane is done with the previous item's state
+    if (lead) {
+      const int4 w = b.items[it];  // member, tile x, tile y, warp
+      const BatchMember &m = b.members[w.x];
+      const int c = (m.cur ^ b.parity) & 1;
+      fill_launch(a, m, c, b.storage, clock);
+    }
+    __syncwarp();
+    const int4 w = b.items[it];
+    run_tile<T, kC, kRows, kS, kReduce, kDual>(
+        a, w.y, w.z, w.w, slot, b.members[w.x].gx, lut, smem);
   }
   // the last block to finish advances the clock for the next launch (every
   // thread read it before its block's first tile)
@@ -1524,7 +1550,8 @@ int choose_variant_t(int64_t nx, int64_t ny) {
 template <typename T, int kV, bool kReduce>
 cudaError_t launch_batch_variant(const BatchLaunch &b, cudaStream_t s) {
   constexpr Variant v = kVariants[kV];
-  constexpr int smem = smem_bytes<T, v.cols, v.stages>();
+  constexpr int smem = batch_smem_bytes<T, v.cols, v.stages>();
+  static_assert(smem <= 227 * 1024, "shared memory per block");
   auto kern =
       lbm_batch_kernel<T, v.cols, v.rows, v.min_blocks, v.stages, kReduce,
                        v.dual>;
