@@ -56,8 +56,9 @@ extern "C" {
 #define LBM_SOLID 1
 #define LBM_FIXED 2
 
-/* Device storage formats.  Arithmetic is FP32 in all of them, and the
- * residual and mass reductions FP64. */
+/* Device storage formats.  Arithmetic is FP32 in all of them; the residual
+ * and mass reductions sum in FP32 per lane (the mass compensated) and in FP64
+ * across lanes and tiles. */
 #define LBM_STORAGE_F32 0  /* rho - 1, jx, jy as float32 (24 B/node, 2 copies) */
 #define LBM_STORAGE_F16 1  /* as IEEE binary16, (rho - 1) * 2^10 and j * 2^6
                               (12 B/node, 2 copies) */
