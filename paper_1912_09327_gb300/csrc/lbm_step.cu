@@ -183,9 +183,8 @@ int dual_variant(int v, int64_t nx, int64_t ny) {
       n = 0;
     return n;
   }();
-  // the clean-tile code pays off once every SM runs a few blocks (measured:
-  // +2 % on a periodic 4096^2 box, +12 to +19 % on 8192^2 and 16384^2
-  // cavities, three blocks per SM)
+  // the clean-tile code pays off once every SM runs a few blocks; on
+  // smaller grids the general code's shorter tiles win
   if (sms <= 0 || launched_blocks(nx, ny, v) < 2 * static_cast<int64_t>(sms))
     return -1;
   for (int i = 0; i < kNumVariants; ++i) {
