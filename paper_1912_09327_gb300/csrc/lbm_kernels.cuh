@@ -1079,9 +1079,9 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
     ist = issued == kS ? 0 : issued;
     __syncwarp();
     // takes ring row i into `r` and refills its stage; false on a timeout
-    auto take = [&](int i, Row &r) -> bool {
-      const bool ok = fetch(i, tst, tph, r);
-      if (!__all_sync(kFull, ok)) return false;
+    // releases the stage of the row just read: refills it with the next ring
+    // row to issue, and advances to the next row to take
+    auto release = [&]() {
       __syncwarp();  // every lane has read the stage
       if (issued < nrows) {
         if (lane == 0) {
@@ -1095,6 +1095,26 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
         tst = 0;
         tph ^= 1u;
       }
+    };
+    auto take = [&](int i, Row &r) -> bool {
+      const bool ok = fetch(i, tst, tph, r);
+      if (!__all_sync(kFull, ok)) return false;
+      release();
+      return true;
+    };
+    // kSC: takes ring row i, which `peeked` was just read from by peek: its
+    // values are in registers already, so only the stage is released
+    auto take_peeked = [&](int i, Row &r, const Row &peeked) -> bool {
+      if constexpr (!kSC) return take(i, r);
+#pragma unroll
+      for (int q = 0; q < kP; ++q) {
+        r.d[q] = peeked.d[q];
+        r.jx[q] = peeked.jx[q];
+        r.jy[q] = peeked.jy[q];
+      }
+      r.solid = peeked.solid;
+      r.fluid = peeked.fluid;
+      release();
       return true;
     };
     // reads the next ring row i (the one after the last taken) into `r`
@@ -1120,9 +1140,11 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
         for (int q = 0; q < kP; ++q) rb.zx[q] = rb.zy[q] = bc(0.f);
       }
     }
+    // kSC: every source row was peeked as the row above the one before it
+    // (the first one before the loop), so it is taken from the registers
     for (int k = 0; k < npairs && failed < 0; ++k) {
       const int r0 = 2 * k + kLead;  // ring row of source row 2k
-      if (!take(r0, ra)) {
+      if (!take_peeked(r0, ra, rn)) {
         failed = r0;
         break;
       }
@@ -1131,7 +1153,7 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
         break;
       }
       row(2 * k, ra, rb, rn, tC0, tA0, tS0, tC1, tA1, tS1);
-      if (!take(r0 + 1, rb)) {
+      if (!take_peeked(r0 + 1, rb, rn)) {
         failed = r0 + 1;
         break;
       }
