@@ -117,6 +117,10 @@ int upload(lbm_batch *b) {
   int64_t tx = 0, ty = 0;
   lbmtau1::variant_tile(b->variant, &tx, &ty);
   b->h_members.resize(n);
+  // A kernel with the clean-tile code takes the work list ordered by tile
+  // kind (below), which depends on the flags.
+  const bool by_kind = lbmtau1::variant_has_clean_code(b->variant);
+  bool flags_changed = false;
   for (int i = 0; i < n; ++i) {
     lbm_ctx *c = b->packed[i];
     BatchMember &m = b->h_members[i];
@@ -144,21 +148,49 @@ int upload(lbm_batch *b) {
           b->stream);
       if (e != cudaSuccess) return bcuda(b, e, "tile flags kernel launch");
       c->clean_variant = b->variant;
+      flags_changed = true;
     }
     m.clean = c->clean;
   }
+  if (by_kind && flags_changed) b->items_dirty = true;
   if (b->items_dirty) {
     b->h_items.clear();
-    for (int i = 0; i < n; ++i) {
-      const BatchMember &m = b->h_members[i];
-      const int64_t gy = m.nblocks / m.gx;
-      // every warp tile of every block tile (vertical neighbours next to
-      // each other, for the rows they share)
-      for (int64_t by = 0; by < gy; ++by)
-        for (int64_t bx = 0; bx < m.gx; ++bx)
-          for (int w = 0; w < lbmtau1::kTileWarps; ++w)
-            b->h_items.push_back(make_int4(i, static_cast<int>(bx),
-                                           static_cast<int>(by), w));
+    // With the clean-tile code in the kernel, the warp tiles that take the
+    // general code come first and the clean ones after them: warps running
+    // the two code paths side by side on an SM stall on instruction fetch
+    // (ncu on the 512-domain mix: 2.4 no-instruction stalls per issue mixed,
+    // 0.65 with the general kernel alone).  The flags are read to the host
+    // once per rebuild of the list.
+    std::vector<std::vector<uint8_t>> flags(by_kind ? n : 0);
+    if (by_kind) {
+      for (int i = 0; i < n; ++i) {
+        flags[i].resize(static_cast<size_t>(b->h_members[i].nblocks) *
+                        lbmtau1::kTileWarps);
+        cudaError_t e = cudaMemcpyAsync(flags[i].data(), b->packed[i]->clean,
+                                        flags[i].size(),
+                                        cudaMemcpyDeviceToHost, b->stream);
+        if (e != cudaSuccess) return bcuda(b, e, "cudaMemcpyAsync(flags)");
+      }
+      cudaError_t e = cudaStreamSynchronize(b->stream);
+      if (e != cudaSuccess) return bcuda(b, e, "cudaStreamSynchronize(flags)");
+    }
+    for (int pass = 0; pass < (by_kind ? 2 : 1); ++pass) {
+      for (int i = 0; i < n; ++i) {
+        const BatchMember &m = b->h_members[i];
+        const int64_t gy = m.nblocks / m.gx;
+        // every warp tile of every block tile (vertical neighbours next to
+        // each other, for the rows they share)
+        for (int64_t by = 0; by < gy; ++by)
+          for (int64_t bx = 0; bx < m.gx; ++bx)
+            for (int w = 0; w < lbmtau1::kTileWarps; ++w) {
+              if (by_kind &&
+                  (flags[i][(by * m.gx + bx) * lbmtau1::kTileWarps + w] != 0) !=
+                      (pass == 1))
+                continue;
+              b->h_items.push_back(make_int4(i, static_cast<int>(bx),
+                                             static_cast<int>(by), w));
+            }
+      }
     }
     const int64_t tiles =
         static_cast<int64_t>(b->h_items.size()) / lbmtau1::kTileWarps;

@@ -141,6 +141,10 @@ void variant_tile(int v, int64_t *tile_x, int64_t *tile_y) {
   *tile_y = static_cast<int64_t>(kWarps) * t.rows;
 }
 
+bool variant_has_clean_code(int v) {
+  return v >= 0 && v < kNumVariants && kVariants[v].dual;
+}
+
 int default_variant() { return active_variant(); }
 
 cudaError_t launch_batch(int v, const BatchLaunch &b, bool reduce,

@@ -107,6 +107,8 @@ extern const StorageOps kOpsF32, kOpsF16, kOpsBF16;
 // default variant of the single-domain path.
 int variant_count();
 void variant_tile(int v, int64_t *tile_x, int64_t *tile_y);
+// True when variant v's kernel carries the clean-tile code (reads the flags).
+bool variant_has_clean_code(int v);
 int default_variant();
 
 // Enqueues one batched step with tile variant v over a persistent grid; the
