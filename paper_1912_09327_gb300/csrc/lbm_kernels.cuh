@@ -1140,9 +1140,22 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
         for (int q = 0; q < kP; ++q) rb.zx[q] = rb.zy[q] = bc(0.f);
       }
     }
+    if constexpr (!kClean && !kSC) {
+      // the general code: one row per loop turn (half the loop's code), the
+      // row just computed copied into the previous-row buffer
+#pragma unroll 1
+      for (int i = 0; i < 2 * npairs; ++i) {
+        if (!take(i, ra)) {
+          failed = i;
+          break;
+        }
+        row(i, ra, rb, rn, tC0, tA0, tS0, tC1, tA1, tS1);
+        rb = ra;
+      }
+    }
     // kSC: every source row was peeked as the row above the one before it
     // (the first one before the loop), so it is taken from the registers
-    for (int k = 0; k < npairs && failed < 0; ++k) {
+    for (int k = 0; (kClean || kSC) && k < npairs && failed < 0; ++k) {
       const int r0 = 2 * k + kLead;  // ring row of source row 2k
       if (!take_peeked(r0, ra, rn)) {
         failed = r0;
