@@ -389,6 +389,12 @@ int64_t lbm_tile_count(int64_t nx, int64_t ny, int32_t variant);
 int lbm_variant_tile(int32_t variant, int64_t *tile_x, int64_t *tile_y,
                      int32_t *cols_per_lane);
 
+/* 1 when a variant's kernel also carries the code for clean warp tiles
+ * (every node of the tile and its one-node halo in the domain and fluid),
+ * which the per-tile flags select; its tiles are those of the variant of the
+ * same shape without it.  0 when it does not, -1 for an invalid variant. */
+int32_t lbm_variant_has_clean_code(int32_t variant);
+
 /* Autotuner: times steps_per_variant (even, >= 2) batch steps, plus two
  * warm-up steps, with every tile variant and keeps the fastest.  These are
  * real steps: every member advances by (steps_per_variant + 2) times the

@@ -114,6 +114,8 @@ _lib.lbm_tile_count.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int32]
 _lib.lbm_tile_count.restype = ctypes.c_int64
 _lib.lbm_variant_tile.argtypes = [ctypes.c_int32, _vp, _vp, _vp]
 _lib.lbm_variant_tile.restype = ctypes.c_int
+_lib.lbm_variant_has_clean_code.argtypes = [ctypes.c_int32]
+_lib.lbm_variant_has_clean_code.restype = ctypes.c_int32
 _lib.lbm_batch_set_variant.argtypes = [_vp, ctypes.c_int32]
 _lib.lbm_batch_set_variant.restype = ctypes.c_int
 _lib.lbm_batch_variant.argtypes = [_vp]
@@ -314,6 +316,13 @@ def lbm_batch_step(b, nsteps) -> None:
 
 def lbm_variant_count() -> int:
     return int(_lib.lbm_variant_count())
+
+
+def lbm_variant_has_clean_code(variant: int) -> bool:
+    r = int(_lib.lbm_variant_has_clean_code(int(variant)))
+    if r < 0:
+        raise LbmError(LBM_E_INVAL, "no tile variant %d" % variant)
+    return r == 1
 
 
 def lbm_variant_tile(variant: int):

@@ -312,6 +312,11 @@ int lbm_variant_tile(int32_t variant, int64_t *tile_x, int64_t *tile_y,
   return LBM_OK;
 }
 
+int32_t lbm_variant_has_clean_code(int32_t variant) {
+  if (variant < 0 || variant >= lbmtau1::variant_count()) return -1;
+  return lbmtau1::variant_has_clean_code(variant) ? 1 : 0;
+}
+
 int64_t lbm_tile_count(int64_t nx, int64_t ny, int32_t variant) {
   if (nx < 1 || ny < 1 || variant < -1 || variant >= lbmtau1::variant_count())
     return -1;

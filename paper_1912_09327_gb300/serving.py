@@ -77,14 +77,19 @@ def choose_batch_variant(shapes):
     marched rows (tile_y plus a halo row above and below each of its four
     warps) times its 32 lanes' columns, two columns per lane costing
     TWO_COLUMN_COST times four per column; the persistent batch kernel takes
-    tiles from one work list, so the waves even out."""
+    tiles from one work list, so the waves even out.  Between two variants
+    of the same tiles, the one whose kernel also carries the clean-tile code
+    wins: its clean tiles skip node types and wall terms, and the batch runs
+    them after the others."""
     best, best_cost = 0, None
     for v in range(binding.lbm_variant_count()):
         tx, ty, cols = binding.lbm_variant_tile(v)
         tiles = sum(binding.lbm_tile_count(nx, ny, v) for nx, ny in shapes)
         cost = tiles * (ty + 8) * 32 * cols * (TWO_COLUMN_COST if cols == 2
                                                else 1.0)
-        if best_cost is None or cost < best_cost:
+        if best_cost is None or cost < best_cost or (
+                cost == best_cost and binding.lbm_variant_has_clean_code(v)
+                and not binding.lbm_variant_has_clean_code(best)):
             best, best_cost = v, cost
     return best
 

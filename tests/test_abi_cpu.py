@@ -142,6 +142,16 @@ def test_call_order_and_arguments_checked_on_host(b):
             assert b.lbm_tile_count(tx + 1, ty + 1, v) == 4
         with pytest.raises(b.LbmError):
             b.lbm_variant_tile(nv)
+        # every variant with the clean-tile code has a twin of the same tiles
+        # without it
+        shapes = {v: b.lbm_variant_tile(v) for v in range(nv)}
+        clean = [v for v in range(nv) if b.lbm_variant_has_clean_code(v)]
+        assert clean and len(clean) < nv
+        for v in clean:
+            assert any(shapes[u] == shapes[v] and
+                       not b.lbm_variant_has_clean_code(u) for u in range(nv))
+        assert lib.lbm_variant_has_clean_code(nv) == -1
+        assert lib.lbm_variant_has_clean_code(-1) == -1
     finally:
         b.lbm_destroy(ctx)
     assert b.lbm_last_error(None) == "null context"

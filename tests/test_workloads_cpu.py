@@ -102,4 +102,6 @@ def test_serving_batch_variant_model():
     assert ty == 64 and cols == 4
     big = serving.choose_batch_variant([(4096, 4096)])
     assert binding.lbm_variant_tile(big)[1] == 256
+    # of the two variants with those tiles, the one with the clean-tile code
+    assert binding.lbm_variant_has_clean_code(big)
     assert 0 <= serving.choose_batch_variant([(1, 1)]) < binding.lbm_variant_count()
