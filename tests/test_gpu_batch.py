@@ -165,6 +165,48 @@ def test_batch_membership_changes(b):
     batch.close()
 
 
+def test_batch_clean_tiles_run_last_and_equal_alone(b):
+    """A batch whose kernel carries the clean-tile code, with members that
+    have clean warp tiles (a 600 x 600 cavity, a 700 x 300 channel) beside
+    small ones, orders its work list by tile kind (general tiles first);
+    every member still reaches the state it reaches alone, bit for bit,
+    also after a member leaves and the list is rebuilt, and after a member's
+    node types change (its flags are computed again)."""
+    import torch
+    stream = torch.cuda.current_stream()
+    dual = [v for v in range(b.lbm_variant_count())
+            if b.lbm_variant_has_clean_code(v)][0]
+    tx, ty, _ = b.lbm_variant_tile(dual)
+    probs = [wl.cavity(600, 0.1), wl.channel(700, 300, 0.01), wl.cavity(40, 0.1),
+             wl.porous(100, seed=2, r_min=3, r_max=8, ny=90, fx=1e-4)]
+    doms = [b.Domain.from_problem(p, stream=stream) for p in probs]
+    batch = b.Batch(len(doms), 100000, stream=stream)
+    slots = [batch.add(d) for d in doms]
+    batch.set_variant(dual)
+    batch.step(15)
+    batch.remove(slots[2])
+    batch.step(10)
+    # new node types for the channel: a solid block in its middle
+    mask = probs[1].mask.copy()
+    mask[100:140, 300:340] = wl.SOLID
+    doms[1].set_geometry(mask)
+    doms[1].set_moments(probs[1].rho, probs[1].jx, probs[1].jy)
+    batch.step(7)
+    counts = [32, 7, 15, 32]
+    for i, (d, p, n) in enumerate(zip(doms, probs, counts)):
+        ref = b.Domain.from_problem(p, stream=stream)
+        if i == 1:
+            ref.set_geometry(mask)
+            ref.set_moments(p.rho, p.jx, p.jy)
+        ref.step(n)
+        for x, y in zip(d.get_state(), ref.get_state()):
+            assert np.array_equal(x, y), i
+        ref.close()
+    batch.close()
+    for d in doms:
+        d.close()
+
+
 def test_batch_member_matches_oracle(b):
     p = wl.random_problem(300, 170, seed=5, periodic=(True, False))
     q = wl.cavity(257, 0.1, ny=133)
