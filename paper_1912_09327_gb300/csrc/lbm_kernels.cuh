@@ -566,7 +566,9 @@ __device__ __forceinline__ void step_tile(const StepLaunch &a, int64_t bx,
       }
       unsigned char *dst = stages + st * St::kBytes;
       unsigned char *dmask = dst + 3 * St::kFieldBytes;
-      if (interior) {  // the whole window lies in the row
+      // the whole window lies in the row, or (clean tile) at most 16 bytes
+      // past its last column, which the lanes do not read
+      if (kClean || interior) {
         const int64_t off = static_cast<int64_t>(r) * a.pitch + ws;
         mbar_expect_tx(bar, 3 * St::kFieldBytes + (kClean ? 0 : St::kMaskBytes));
         bulk_copy(dst, static_cast<const T *>(a.src.d) + off, St::kFieldBytes,
