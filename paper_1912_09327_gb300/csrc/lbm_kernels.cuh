@@ -31,7 +31,8 @@
 // that row with the packed FP32 instructions (FADD2 / FMUL2 / FFMA2), in the
 // order the vector loads deliver them.  Each source row is read from HBM
 // once, turned into per-node quantities once (one reciprocal per node), its
-// left/right neighbour columns come from warp shuffles, and its contributions
+// left/right neighbour columns come from warp shuffles (their sums and
+// differences formed column by column), and its contributions
 // are added to the output rows it feeds (above, same, below); one output row
 // completes per source row and is stored as vectors.  Interior warp
 // tiles stream their row windows through a ring of shared-memory stages
@@ -39,9 +40,9 @@
 // every wait bounded in time), several rows ahead of use; at the domain's
 // edges the copies are clipped to the row and a periodic axis's wrapped
 // column arrives as one more 16-byte block.  On the last step of an lbm_step call the
-// same kernel reduces sum |du|^2, sum |u|^2 and sum delta (warp shuffles, one
-// FP64 partial per warp tile) and raises a sticky flag on rho <= 0 or
-// non-finite values.
+// same kernel reduces sum |du|^2, sum |u|^2 and sum delta (FP32 per lane, the
+// mass compensated, then FP64 warp shuffles into one partial per warp tile)
+// and raises a sticky flag on rho <= 0 or non-finite values.
 // The storage type T (FP32, or FP16 / BF16 deviations) only changes loads and
 // stores; the arithmetic is FP32 throughout.  A batched kernel runs the same
 // tile code, warp by warp, over a work list of many domains' warp tiles.
@@ -454,8 +455,10 @@ __host__ __device__ constexpr int batch_smem_bytes() {
 //   out(s - 1) = South(s - 2) + Same(s - 1) + North(s),
 // and the warp carries acc = South(s - 2) + Same(s - 1) and South(s - 1)
 // from one row to the next, with the raw row s - 1 (the old values of the
-// nodes it completes).  Rows are taken two per loop turn with the roles of
-// the two row buffers swapped, so carrying them costs no register moves.
+// nodes it completes).  Clean tiles (and the multiphase step) take rows two
+// per loop turn with the roles of the two row buffers swapped, so carrying
+// them costs no register moves; the general code takes one row per turn and
+// copies it into the previous-row buffer, which halves its loop's code.
 //
 // warp w (0 .. kWarps - 1, stacked in y) of block tile (bx, by) covers
 // (30 kC) columns x kRows rows.  `gx` is the number of block tiles along x
