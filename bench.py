@@ -339,7 +339,7 @@ def run_precision(binding, stream, max_steps=60000, chunk=5000):
     return out
 
 
-def run_e2e(binding, dom, n, steps, lanes=3):
+def run_e2e(binding, dom, n, steps, lanes=2):
     """Same metric through the public API with host buffers: per step, the
     exact state goes host -> device from pinned memory (lbm_set_state), one
     lbm_step, the state comes back (lbm_get_state) and the residual is read
